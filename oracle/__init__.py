@@ -1,0 +1,215 @@
+"""EPO FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Thin ctypes wrapper over ``epo_oracle.c`` (plain C, double precision, OpenMP over
+pairs with a fixed-order final reduction).  Only ``tests/``, the smoke check and the
+CPU-baseline leg of ``bench.py`` may import this package; the CUDA library and its
+Python binding never do.
+
+What it computes (Section 3 and the appendix algorithms):
+  * ``edt`` / ``edt_brute``: the distance transform field DTF_i (Algorithm 1,
+    ComputeDistanceFields), exact L2 (Felzenszwalb-Huttenlocher) and brute force;
+  * ``loss_grad``: the edge reprojection loss (Eqs. 6-8) with per-pair statistics and
+    the analytic left-perturbation pose gradient;
+  * ``optimize``: the optimisation loop of Algorithm 2 restricted to poses (lambda
+    anneal of Algorithm 3, tangent-space Adam, Exp retraction);
+  * ``se3_exp`` / ``se3_log`` / ``se3_left_jacobian`` and ``robust``.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "epo_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_epo_oracle.so")
+_lib = None
+
+NORM_VALID = 0
+NORM_ALL = 1
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("W", ctypes.c_void_p), ("H", ctypes.c_void_p),
+                ("K", ctypes.c_void_p), ("rec_off", ctypes.c_void_p), ("rec", ctypes.c_void_p),
+                ("map_off", ctypes.c_void_p), ("map", ctypes.c_void_p), ("n_pairs", ctypes.c_int),
+                ("pairs", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("delta", ctypes.c_double), ("eps_z", ctypes.c_double),
+                ("norm_mode", ctypes.c_int), ("near_margin", ctypes.c_double)]
+
+
+class _Opt(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("lambda1", ctypes.c_double),
+                ("lambda_steps", ctypes.c_int), ("delta", ctypes.c_double),
+                ("eps_z", ctypes.c_double), ("norm_mode", ctypes.c_int),
+                ("lr_rot", ctypes.c_double), ("lr_trans", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        lib.oracle_edt.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
+        lib.oracle_edt_brute.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
+        lib.oracle_robust.argtypes = [ctypes.c_double] * 3 + [P, P]
+        lib.oracle_robust.restype = None
+        lib.oracle_loss_grad.argtypes = [P, P, P, P, P, P, P, P]
+        lib.oracle_se3_exp.argtypes = [P, P]
+        lib.oracle_se3_exp.restype = None
+        lib.oracle_se3_log.argtypes = [P, P]
+        lib.oracle_se3_log.restype = None
+        lib.oracle_se3_left_jacobian.argtypes = [P, P]
+        lib.oracle_se3_left_jacobian.restype = None
+        lib.oracle_lambda.argtypes = [P, ctypes.c_int64]
+        lib.oracle_lambda.restype = ctypes.c_double
+        lib.oracle_optimize.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------------------------------------
+def edt(edge: np.ndarray) -> np.ndarray:
+    """Exact Euclidean distance (pixels) to the nearest nonzero pixel of ``edge`` (H, W)."""
+    e = np.ascontiguousarray(edge, dtype=np.uint8)
+    H, W = e.shape
+    out = np.empty((H, W), dtype=np.float64)
+    rc = _load().oracle_edt(_p(e), W, H, _p(out))
+    if rc:
+        raise RuntimeError(f"oracle_edt failed ({rc})")
+    return out
+
+
+def edt_brute(edge: np.ndarray) -> np.ndarray:
+    e = np.ascontiguousarray(edge, dtype=np.uint8)
+    H, W = e.shape
+    out = np.empty((H, W), dtype=np.float64)
+    _load().oracle_edt_brute(_p(e), W, H, _p(out))
+    return out
+
+
+def robust(d: float, lam: float, delta: float):
+    """(rho, drho) = (H_delta(min(d, lambda)), gradient passed through the clamp)."""
+    r = np.zeros(1)
+    g = np.zeros(1)
+    _load().oracle_robust(float(d), float(lam), float(delta), _p(r), _p(g))
+    return float(r[0]), float(g[0])
+
+
+def se3_exp(xi) -> np.ndarray:
+    x = np.ascontiguousarray(xi, dtype=np.float64).reshape(6)
+    T = np.zeros(12)
+    _load().oracle_se3_exp(_p(x), _p(T))
+    return T
+
+
+def se3_log(T) -> np.ndarray:
+    t = np.ascontiguousarray(T, dtype=np.float64).reshape(12)
+    xi = np.zeros(6)
+    _load().oracle_se3_log(_p(t), _p(xi))
+    return xi
+
+
+def se3_left_jacobian(xi) -> np.ndarray:
+    x = np.ascontiguousarray(xi, dtype=np.float64).reshape(6)
+    J = np.zeros(36)
+    _load().oracle_se3_left_jacobian(_p(x), _p(J))
+    return J.reshape(6, 6)
+
+
+class OracleScene:
+    """Scene in the oracle's flat FP64 layout.
+
+    rec: (n_rec, >=3) (u, v, z) -- pass the values the GPU stores (already rounded).
+    maps: list of (H, W) arrays -- pass the values the GPU stores (already rounded).
+    """
+
+    def __init__(self, W: Sequence[int], H: Sequence[int], K: np.ndarray, rec_off: np.ndarray,
+                 rec: np.ndarray, maps: Sequence[np.ndarray], pairs: np.ndarray):
+        self.W = np.ascontiguousarray(W, dtype=np.int32)
+        self.H = np.ascontiguousarray(H, dtype=np.int32)
+        self.K = np.ascontiguousarray(K, dtype=np.float64).reshape(-1, 4)
+        self.rec_off = np.ascontiguousarray(rec_off, dtype=np.int64)
+        self.rec = np.ascontiguousarray(np.asarray(rec, dtype=np.float64)[:, :3])
+        self.map_off = np.zeros(len(maps), dtype=np.int64)
+        off = 0
+        for v, m in enumerate(maps):
+            self.map_off[v] = off
+            off += m.size
+        self.map = np.ascontiguousarray(np.concatenate([np.asarray(m, np.float64).reshape(-1) for m in maps])
+                                        if maps else np.zeros(1))
+        self.pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        self.n_views = len(self.W)
+        self.n_pairs = self.pairs.shape[0]
+        self._s = _Scene(self.n_views, self.W.ctypes.data, self.H.ctypes.data, self.K.ctypes.data,
+                         self.rec_off.ctypes.data, self.rec.ctypes.data, self.map_off.ctypes.data,
+                         self.map.ctypes.data, self.n_pairs, self.pairs.ctypes.data)
+
+    def loss_grad(self, T: np.ndarray, lam: float, delta: float = 1.0, eps_z: float = 1e-6,
+                  norm_mode: int = NORM_VALID, near_margin: float = 1e-3):
+        """Returns dict(loss, grad (n,6), pair_stats (P,8), pair_near (P,), pair_loss (P,))."""
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12)
+        prm = _Params(lam, delta, eps_z, norm_mode, near_margin)
+        loss = np.zeros(1)
+        grad = np.zeros((self.n_views, 6))
+        P = max(self.n_pairs, 1)
+        st = np.zeros((P, 8))
+        near = np.zeros(P, dtype=np.int64)
+        pl = np.zeros(P)
+        rc = _load().oracle_loss_grad(ctypes.byref(self._s), _p(T), ctypes.byref(prm), _p(loss), _p(grad),
+                                      _p(st), _p(near), _p(pl))
+        if rc:
+            raise ValueError(f"oracle_loss_grad failed ({rc})")
+        return dict(loss=float(loss[0]), grad=grad, pair_stats=st[:self.n_pairs],
+                    pair_near=near[:self.n_pairs], pair_loss=pl[:self.n_pairs])
+
+    def optimize(self, T: np.ndarray, fixed: np.ndarray, n_steps: int, *, lambda0=10.0, lambda1=6.0,
+                 lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID, lr_rot=1e-3,
+                 lr_trans=1e-2, beta1=0.9, beta2=0.999, eps=1e-12, step0=0, m=None, v=None):
+        """Run n_steps of Algorithm 2 (pose-only, tangent-space Adam).  Returns (T, m, v, losses)."""
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12).copy()
+        fx = np.ascontiguousarray(fixed, dtype=np.uint8)
+        m = np.zeros((self.n_views, 6)) if m is None else np.ascontiguousarray(m, np.float64).copy()
+        v = np.zeros((self.n_views, 6)) if v is None else np.ascontiguousarray(v, np.float64).copy()
+        hist = np.zeros(max(n_steps, 1))
+        opt = _Opt(lambda0, lambda1, lambda_steps, delta, eps_z, norm_mode, lr_rot, lr_trans, beta1,
+                   beta2, eps)
+        rc = _load().oracle_optimize(ctypes.byref(self._s), _p(T), _p(fx), ctypes.byref(opt), step0,
+                                     n_steps, _p(m), _p(v), _p(hist))
+        if rc:
+            raise ValueError(f"oracle_optimize failed ({rc})")
+        return T, m, v, hist[:n_steps]
+
+
+def lambda_at(step: int, lambda0=10.0, lambda1=6.0, lambda_steps=1000) -> float:
+    opt = _Opt(lambda0, lambda1, lambda_steps, 1.0, 1e-6, 0, 0, 0, 0.9, 0.999, 1e-12)
+    return float(_load().oracle_lambda(ctypes.byref(opt), step))
+
+
+def scene_from_synth(sc, maps, rec=None) -> OracleScene:
+    """Oracle scene from a ``synth.Scene`` and per-view maps (values the GPU stores)."""
+    r = sc.rec if rec is None else rec
+    return OracleScene(sc.W, sc.H, sc.K, sc.rec_off, r, maps, sc.pairs)

@@ -1,0 +1,563 @@
+/*
+ * EPO FP64 CPU ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously-correct double-precision restatement of the EPO
+ * edge-alignment objective (Section 3, Eqs. 6-8) and its analytic pose
+ * gradient, the distance transform field it samples (Section 3, Algorithm 1,
+ * "ComputeDistanceFields"), and the pose update used by the optimisation
+ * loop (Algorithm 2, with the tangent-space Adam reading stated below).
+ * Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no source with the CUDA library.
+ *
+ * Readings of points the paper leaves open (each is repeated at its use):
+ *   - Pose T = [R|t] maps world -> camera (the extrinsic P of Section 3).
+ *   - Depth is z-depth; pixel centres sit at integer coordinates.
+ *   - A projected sample is valid iff Y3 > eps_z and 0 <= u' <= W-1 and
+ *     0 <= v' <= H-1 (no occlusion test; the paper has none).
+ *   - Bilinear cell: x0 = min(floor(u'), W-2), y0 = min(floor(v'), H-2).
+ *   - Huber H_delta(x) = x^2/2 for |x| <= delta, delta(|x| - delta/2) else;
+ *     the clamp d^ = min(d, lambda) passes the gradient when d <= lambda.
+ *   - Per-direction mean: sum(rho) / sum(valid) (Algorithm 3) by default,
+ *     or sum(rho) / |E_i| (Eq. 7) when norm_mode == 1.
+ *   - Directed pair list of length P: L = (2/P) * sum_p l_p, which equals
+ *     Eq. 6 for a symmetric list (every undirected pair counted both ways).
+ *   - Pose gradient is taken w.r.t. a left perturbation T <- Exp(xi) T with
+ *     xi = (upsilon, omega), translation first.
+ *
+ * Precision: every value is double; inputs that the GPU stores in reduced
+ * precision are passed here already rounded and widened.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL 1
+#define ORACLE_ENOMEM 3
+
+/* ------------------------------------------------------------------ */
+/* Distance transform field (Section 3; exact L2 EDT of Felzenszwalb   */
+/* and Huttenlocher, "Distance transforms of sampled functions").      */
+/* ------------------------------------------------------------------ */
+
+/* 1-D squared distance transform of f over n samples: d(q) = min_p (q - p)^2 + f(p),
+ * computed as the lower envelope of parabolas (Felzenszwalb-Huttenlocher).
+ * Samples with f >= INF add no parabola.  v, z are work arrays of n and n+1 entries. */
+static void edt_1d(const double* f, int n, double* d, int* v, double* z) {
+  const double INF = 1e300;
+  int q0 = 0;
+  while (q0 < n && f[q0] >= INF) ++q0;
+  if (q0 == n) {
+    for (int q = 0; q < n; ++q) d[q] = INF;
+    return;
+  }
+  int k = 0;
+  v[0] = q0;
+  z[0] = -INF;
+  z[1] = INF;
+  for (int q = q0 + 1; q < n; ++q) {
+    if (f[q] >= INF) continue;
+    double s = ((f[q] + (double)q * q) - (f[v[k]] + (double)v[k] * v[k])) / (2.0 * q - 2.0 * v[k]);
+    while (s <= z[k]) {
+      --k;
+      s = ((f[q] + (double)q * q) - (f[v[k]] + (double)v[k] * v[k])) / (2.0 * q - 2.0 * v[k]);
+    }
+    ++k;
+    v[k] = q;
+    z[k] = s;
+    z[k + 1] = INF;
+  }
+  k = 0;
+  for (int q = 0; q < n; ++q) {
+    while (z[k + 1] < q) ++k;
+    double dq = (double)q - v[k];
+    d[q] = dq * dq + f[v[k]];
+  }
+}
+
+/* dist[y*W + x] = Euclidean distance from pixel (x, y) to the nearest edge
+ * pixel; a view without edges gets W + H everywhere. */
+int oracle_edt(const uint8_t* edge, int W, int H, double* dist) {
+  if (W < 1 || H < 1) return ORACLE_EINVAL;
+  int any = 0;
+  for (int64_t o = 0; o < (int64_t)W * H; ++o) any |= edge[o];
+  if (!any) {
+    for (int64_t o = 0; o < (int64_t)W * H; ++o) dist[o] = (double)(W + H);
+    return ORACLE_OK;
+  }
+  int n = W > H ? W : H;
+  double* f = (double*)malloc(sizeof(double) * n);
+  double* d = (double*)malloc(sizeof(double) * n);
+  double* z = (double*)malloc(sizeof(double) * (n + 1));
+  int* v = (int*)malloc(sizeof(int) * n);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)W * H);
+  if (!f || !d || !z || !v || !tmp) {
+    free(f); free(d); free(z); free(v); free(tmp);
+    return ORACLE_ENOMEM;
+  }
+  const double INF = 1e300;
+  /* rows */
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) f[x] = edge[(size_t)y * W + x] ? 0.0 : INF;
+    edt_1d(f, W, d, v, z);
+    for (int x = 0; x < W; ++x) tmp[(size_t)y * W + x] = d[x];
+  }
+  /* columns */
+  for (int x = 0; x < W; ++x) {
+    for (int y = 0; y < H; ++y) f[y] = tmp[(size_t)y * W + x];
+    edt_1d(f, H, d, v, z);
+    for (int y = 0; y < H; ++y) dist[(size_t)y * W + x] = sqrt(d[y]);
+  }
+  free(f); free(d); free(z); free(v); free(tmp);
+  return ORACLE_OK;
+}
+
+/* Brute-force EDT: min over all edge pixels, for tiny images. */
+int oracle_edt_brute(const uint8_t* edge, int W, int H, double* dist) {
+  int any = 0;
+  for (int64_t o = 0; o < (int64_t)W * H; ++o) any |= edge[o];
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      if (!any) { dist[(size_t)y * W + x] = (double)(W + H); continue; }
+      double best = 1e300;
+      for (int yy = 0; yy < H; ++yy)
+        for (int xx = 0; xx < W; ++xx)
+          if (edge[(size_t)yy * W + xx]) {
+            double dd = (double)(x - xx) * (x - xx) + (double)(y - yy) * (y - yy);
+            if (dd < best) best = dd;
+          }
+      dist[(size_t)y * W + x] = sqrt(best);
+    }
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Robust penalty (Eq. 7): Huber of the clamped distance.               */
+/* ------------------------------------------------------------------ */
+static double huber(double x, double delta) {
+  double ax = fabs(x);
+  return ax <= delta ? 0.5 * x * x : delta * (ax - 0.5 * delta);
+}
+static double huber_prime(double x, double delta) {
+  if (fabs(x) <= delta) return x;
+  return x > 0 ? delta : -delta;
+}
+/* rho = H(min(d, lambda)); drho = dH/dd with the clamp passing the gradient
+ * for d <= lambda and blocking it above. */
+void oracle_robust(double d, double lambda, double delta, double* rho, double* drho) {
+  double dh = d < lambda ? d : lambda;
+  *rho = huber(dh, delta);
+  *drho = d <= lambda ? huber_prime(d, delta) : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Scene description (flat arrays, all double)                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int n_views;
+  const int* W;
+  const int* H;
+  const double* K;        /* n_views x 4: fx fy cx cy */
+  const int64_t* rec_off; /* n_views + 1 */
+  const double* rec;      /* n_rec x 3: u v z */
+  const int64_t* map_off; /* n_views: offset of view's W*H map */
+  const double* map;
+  int n_pairs;
+  const int* pairs;       /* 2 x n_pairs interleaved: (i, j) */
+} oracle_scene;
+
+typedef struct {
+  double lambda, delta, eps_z;
+  int norm_mode;          /* 0: sum(valid) (Algorithm 3), 1: |E_i| (Eq. 7) */
+  double near_margin;     /* pixel distance from a validity boundary counted as "near" */
+} oracle_params;
+
+static void mat3_vec(const double* T, const double X[3], double Y[3]) {
+  /* Y = R X + t for T = [R|t] row-major 3x4 */
+  for (int r = 0; r < 3; ++r)
+    Y[r] = T[4 * r] * X[0] + T[4 * r + 1] * X[1] + T[4 * r + 2] * X[2] + T[4 * r + 3];
+}
+
+/* UnprojectEdgesTo3D (Algorithm 2): X_world = P^-1 K^-1 [u, v, 1]^T z.
+ * With P = [R|t], P^-1 X_c = R^T (X_c - t). */
+static void unproject(const double* K, const double* T, const double* rec, double Xc[3],
+                      double Xw[3]) {
+  double u = rec[0], v = rec[1], z = rec[2];
+  Xc[0] = (u - K[2]) / K[0] * z;
+  Xc[1] = (v - K[3]) / K[1] * z;
+  Xc[2] = z;
+  double q[3] = {Xc[0] - T[3], Xc[1] - T[7], Xc[2] - T[11]};
+  for (int c = 0; c < 3; ++c) Xw[c] = T[c] * q[0] + T[4 + c] * q[1] + T[8 + c] * q[2];
+}
+
+/*
+ * Per-pair accumulation for one directed pair (i -> j) (Eq. 8 and the
+ * summand of Eq. 7).  stats[0] = sum rho, stats[1] = n_valid,
+ * stats[2..4] = sum dRho/dY (frame j), stats[5..7] = sum Y x dRho/dY,
+ * gi[6], gj[6] = un-normalised pose-gradient sums for views i and j,
+ * *near = samples whose validity lies within near_margin of flipping.
+ */
+static void pair_terms(const oracle_scene* S, const double* T, const double* Xw_all,
+                       const oracle_params* prm, int p, double stats[8], double gi[6],
+                       double gj[6], int64_t* near) {
+  int i = S->pairs[2 * p], j = S->pairs[2 * p + 1];
+  const double* Ti = T + 12 * i;
+  const double* Tj = T + 12 * j;
+  const double* Ki = S->K + 4 * i;
+  const double* Kj = S->K + 4 * j;
+  int Wj = S->W[j], Hj = S->H[j];
+  const double* map = S->map + S->map_off[j];
+  double fx = Kj[0], fy = Kj[1], cx = Kj[2], cy = Kj[3];
+  for (int k = 0; k < 8; ++k) stats[k] = 0.0;
+  for (int k = 0; k < 6; ++k) gi[k] = gj[k] = 0.0;
+  *near = 0;
+  for (int64_t r = S->rec_off[i]; r < S->rec_off[i + 1]; ++r) {
+    const double* Xw = Xw_all + 3 * r;
+    double Y[3];
+    mat3_vec(Tj, Xw, Y); /* second half of pi: world -> camera j */
+    double up = 0, vp = 0;
+    int in_front = Y[2] > prm->eps_z;
+    if (fabs(Y[2] - prm->eps_z) <= 1e-9 * (1.0 + fabs(Y[2]))) ++*near;
+    if (!in_front) continue;
+    up = fx * Y[0] / Y[2] + cx;
+    vp = fy * Y[1] / Y[2] + cy;
+    double m = prm->near_margin;
+    if (fabs(up) <= m || fabs(up - (Wj - 1)) <= m || fabs(vp) <= m || fabs(vp - (Hj - 1)) <= m)
+      ++*near;
+    if (!(up >= 0.0 && up <= Wj - 1 && vp >= 0.0 && vp <= Hj - 1)) continue;
+    /* bilinear sample of DTF_j */
+    int x0 = (int)floor(up);
+    if (x0 > Wj - 2) x0 = Wj - 2;
+    int y0 = (int)floor(vp);
+    if (y0 > Hj - 2) y0 = Hj - 2;
+    double a = up - x0, b = vp - y0;
+    double m00 = map[(int64_t)y0 * Wj + x0];
+    double m01 = map[(int64_t)y0 * Wj + x0 + 1];
+    double m10 = map[(int64_t)(y0 + 1) * Wj + x0];
+    double m11 = map[(int64_t)(y0 + 1) * Wj + x0 + 1];
+    double d = (1 - a) * (1 - b) * m00 + a * (1 - b) * m01 + (1 - a) * b * m10 + a * b * m11;
+    double dd_du = (1 - b) * (m01 - m00) + b * (m11 - m10);
+    double dd_dv = (1 - a) * (m10 - m00) + a * (m11 - m01);
+    double rho, drho;
+    oracle_robust(d, prm->lambda, prm->delta, &rho, &drho);
+    stats[0] += rho;
+    stats[1] += 1.0;
+    /* chain rule to Y (camera-j coordinates) */
+    double z = Y[2];
+    double gY[3];
+    gY[0] = drho * dd_du * fx / z;
+    gY[1] = drho * dd_dv * fy / z;
+    gY[2] = -drho * (dd_du * fx * Y[0] + dd_dv * fy * Y[1]) / (z * z);
+    double c[3] = {Y[1] * gY[2] - Y[2] * gY[1], Y[2] * gY[0] - Y[0] * gY[2],
+                   Y[0] * gY[1] - Y[1] * gY[0]};
+    for (int k = 0; k < 3; ++k) {
+      stats[2 + k] += gY[k];
+      stats[5 + k] += c[k];
+      gj[k] += gY[k];
+      gj[3 + k] += c[k];
+    }
+    /* view i: Y = R_j R_i^T (X_c - t_i) + t_j, X_c the camera-i lift.
+     * A left perturbation of T_i moves X_c by -(upsilon + omega x X_c) in
+     * camera i, so dRho/dxi_i = (-h, -X_c x h), h = R_i R_j^T gY. */
+    double Xc[3];
+    {
+      const double* rec = S->rec + 3 * r;
+      Xc[0] = (rec[0] - Ki[2]) / Ki[0] * rec[2];
+      Xc[1] = (rec[1] - Ki[3]) / Ki[1] * rec[2];
+      Xc[2] = rec[2];
+    }
+    double w[3]; /* R_j^T gY */
+    for (int c2 = 0; c2 < 3; ++c2) w[c2] = Tj[c2] * gY[0] + Tj[4 + c2] * gY[1] + Tj[8 + c2] * gY[2];
+    double h[3]; /* R_i w */
+    for (int r2 = 0; r2 < 3; ++r2) h[r2] = Ti[4 * r2] * w[0] + Ti[4 * r2 + 1] * w[1] + Ti[4 * r2 + 2] * w[2];
+    double xh[3] = {Xc[1] * h[2] - Xc[2] * h[1], Xc[2] * h[0] - Xc[0] * h[2],
+                    Xc[0] * h[1] - Xc[1] * h[0]};
+    for (int k = 0; k < 3; ++k) {
+      gi[k] -= h[k];
+      gi[3 + k] -= xh[k];
+    }
+  }
+}
+
+/*
+ * Objective and gradient (Eqs. 6-8).  T: n_views x 12.  Outputs:
+ *   loss (scalar), grad (n_views x 6, may be NULL), pair_stats (P x 8, may be
+ *   NULL), pair_near (P, may be NULL), pair_loss (P, may be NULL).
+ */
+int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params* prm,
+                     double* loss, double* grad, double* pair_stats, int64_t* pair_near,
+                     double* pair_loss) {
+  if (!S || !T || !prm || !loss) return ORACLE_EINVAL;
+  int n = S->n_views, P = S->n_pairs;
+  for (int p = 0; p < P; ++p) {
+    int i = S->pairs[2 * p], j = S->pairs[2 * p + 1];
+    if (i < 0 || i >= n || j < 0 || j >= n) return ORACLE_EINVAL;
+  }
+  int64_t n_rec = S->rec_off[n];
+  double* Xw = (double*)malloc(sizeof(double) * 3 * (n_rec > 0 ? n_rec : 1));
+  double* st = (double*)malloc(sizeof(double) * 8 * (P > 0 ? P : 1));
+  double* gi = (double*)malloc(sizeof(double) * 6 * (P > 0 ? P : 1));
+  double* gj = (double*)malloc(sizeof(double) * 6 * (P > 0 ? P : 1));
+  int64_t* nr = (int64_t*)malloc(sizeof(int64_t) * (P > 0 ? P : 1));
+  if (!Xw || !st || !gi || !gj || !nr) {
+    free(Xw); free(st); free(gi); free(gj); free(nr);
+    return ORACLE_ENOMEM;
+  }
+  /* UnprojectEdgesTo3D: once per view (Algorithm 2) */
+  for (int v = 0; v < n; ++v)
+    for (int64_t r = S->rec_off[v]; r < S->rec_off[v + 1]; ++r) {
+      double Xc[3];
+      unproject(S->K + 4 * v, T + 12 * v, S->rec + 3 * r, Xc, Xw + 3 * r);
+    }
+  /* ProjectSampleHuber for every directed pair */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int p = 0; p < P; ++p) pair_terms(S, T, Xw, prm, p, st + 8 * p, gi + 6 * p, gj + 6 * p, nr + p);
+  /* per-direction means and the pair average, in fixed order */
+  double L = 0.0;
+  if (grad)
+    for (int k = 0; k < 6 * n; ++k) grad[k] = 0.0;
+  for (int p = 0; p < P; ++p) {
+    int i = S->pairs[2 * p], j = S->pairs[2 * p + 1];
+    double denom = prm->norm_mode == 1 ? (double)(S->rec_off[i + 1] - S->rec_off[i]) : st[8 * p + 1];
+    double lp = denom > 0 ? st[8 * p] / denom : 0.0;
+    double c = denom > 0 ? (2.0 / P) / denom : 0.0;
+    L += lp;
+    if (pair_loss) pair_loss[p] = lp;
+    if (grad)
+      for (int k = 0; k < 6; ++k) {
+        grad[6 * i + k] += c * gi[6 * p + k];
+        grad[6 * j + k] += c * gj[6 * p + k];
+      }
+    if (pair_stats)
+      for (int k = 0; k < 8; ++k) pair_stats[8 * p + k] = st[8 * p + k];
+    if (pair_near) pair_near[p] = nr[p];
+  }
+  *loss = P > 0 ? (2.0 / P) * L : 0.0;
+  free(Xw); free(st); free(gi); free(gj); free(nr);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* SE(3): exponential, logarithm, left Jacobian (textbook Lie algebra;  */
+/* xi = (upsilon, omega), translation first).                           */
+/* ------------------------------------------------------------------ */
+static void hat(const double w[3], double M[9]) {
+  M[0] = 0; M[1] = -w[2]; M[2] = w[1];
+  M[3] = w[2]; M[4] = 0; M[5] = -w[0];
+  M[6] = -w[1]; M[7] = w[0]; M[8] = 0;
+}
+static void mm3(const double* A, const double* B, double* C) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A[3 * r + k] * B[3 * k + c];
+      C[3 * r + c] = s;
+    }
+}
+
+/* Exp(xi) as a row-major 3x4 [R|t]:
+ * R = I + A W + B W^2, t = (I + B W + C W^2) upsilon, with
+ * A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3, W = omega^. */
+void oracle_se3_exp(const double xi[6], double T[12]) {
+  const double* ups = xi;
+  const double* w = xi + 3;
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double th = sqrt(th2);
+  double A, B, C;
+  if (th < 1e-4) {
+    A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+    B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+  } else {
+    A = sin(th) / th;
+    B = (1.0 - cos(th)) / th2;
+    C = (th - sin(th)) / (th2 * th);
+  }
+  double Wm[9], W2[9];
+  hat(w, Wm);
+  mm3(Wm, Wm, W2);
+  for (int r = 0; r < 3; ++r) {
+    double tr = 0;
+    for (int c = 0; c < 3; ++c) {
+      double I = r == c ? 1.0 : 0.0;
+      T[4 * r + c] = I + A * Wm[3 * r + c] + B * W2[3 * r + c];
+      tr += (I + B * Wm[3 * r + c] + C * W2[3 * r + c]) * ups[c];
+    }
+    T[4 * r + 3] = tr;
+  }
+}
+
+/* Log of a rigid transform (inverse of oracle_se3_exp for rotation angles < pi). */
+void oracle_se3_log(const double T[12], double xi[6]) {
+  double R[9] = {T[0], T[1], T[2], T[4], T[5], T[6], T[8], T[9], T[10]};
+  double c = (R[0] + R[4] + R[8] - 1.0) / 2.0;
+  if (c > 1.0) c = 1.0;
+  if (c < -1.0) c = -1.0;
+  double th = acos(c);
+  double w[3];
+  double vee[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};
+  if (th < 1e-4) {
+    double f = 0.5 * (1.0 + th * th / 6.0);
+    for (int k = 0; k < 3; ++k) w[k] = f * vee[k];
+  } else if (th > 3.14159265358979 - 1e-6) {
+    /* near pi: omega from the symmetric part (R + I)/2 = n n^T */
+    int k = 0;
+    if (R[4] > R[3 * k + k]) k = 1;
+    if (R[8] > R[3 * k + k]) k = 2;
+    double n[3];
+    double s = sqrt((R[3 * k + k] + 1.0) / 2.0);
+    for (int q = 0; q < 3; ++q) n[q] = (q == k) ? s : (R[3 * k + q] + R[3 * q + k]) / (4.0 * s);
+    double sgn = (n[0] * vee[0] + n[1] * vee[1] + n[2] * vee[2]) < 0 ? -1.0 : 1.0;
+    for (int q = 0; q < 3; ++q) w[q] = sgn * th * n[q];
+  } else {
+    double f = th / (2.0 * sin(th));
+    for (int k2 = 0; k2 < 3; ++k2) w[k2] = f * vee[k2];
+  }
+  /* upsilon = V^-1 t,  V^-1 = I - W/2 + (1/th^2)(1 - A/(2B)) W^2 */
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double thh = sqrt(th2);
+  double D;
+  if (thh < 1e-4) {
+    D = 1.0 / 12.0 + th2 / 720.0;
+  } else {
+    double A = sin(thh) / thh, B = (1.0 - cos(thh)) / th2;
+    D = (1.0 - A / (2.0 * B)) / th2;
+  }
+  double Wm[9], W2[9];
+  hat(w, Wm);
+  mm3(Wm, Wm, W2);
+  double t[3] = {T[3], T[7], T[11]};
+  for (int r = 0; r < 3; ++r) {
+    double s = 0;
+    for (int c2 = 0; c2 < 3; ++c2) {
+      double I = r == c2 ? 1.0 : 0.0;
+      s += (I - 0.5 * Wm[3 * r + c2] + D * W2[3 * r + c2]) * t[c2];
+    }
+    xi[r] = s;
+  }
+  for (int k = 0; k < 3; ++k) xi[3 + k] = w[k];
+}
+
+/* Left Jacobian of SE(3), J (6x6 row-major) with Exp(xi + e) ~ Exp(J e) Exp(xi):
+ * J = [[Jw, Q], [0, Jw]], Jw = I + B W + C W^2 (SO(3) left Jacobian) and
+ * Q(upsilon, omega) the translation-rotation coupling block (Barfoot,
+ * "State Estimation for Robotics", Sec. 7.1.5). */
+void oracle_se3_left_jacobian(const double xi[6], double J[36]) {
+  const double* ups = xi;
+  const double* w = xi + 3;
+  double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double th = sqrt(th2);
+  double B, C, c1, c2, c3;
+  if (th < 0.05) {
+    double t4 = th2 * th2;
+    B = 0.5 - th2 / 24.0 + t4 / 720.0;
+    C = 1.0 / 6.0 - th2 / 120.0 + t4 / 5040.0;
+    c1 = 1.0 / 6.0 - th2 / 120.0 + t4 / 5040.0;
+    c2 = 1.0 / 24.0 - th2 / 720.0 + t4 / 40320.0;
+    c3 = 1.0 / 120.0 - th2 / 2520.0 + t4 / 120960.0;
+  } else {
+    double s = sin(th), c = cos(th);
+    B = (1.0 - c) / th2;
+    C = (th - s) / (th2 * th);
+    c1 = (th - s) / (th2 * th);
+    c2 = (th2 / 2.0 + c - 1.0) / (th2 * th2);
+    c3 = (2.0 * th - 3.0 * s + th * c) / (2.0 * th2 * th2 * th);
+  }
+  double Wm[9], W2[9], P[9];
+  hat(w, Wm);
+  mm3(Wm, Wm, W2);
+  hat(ups, P);
+  double WP[9], PW[9], WPW[9], WWP[9], PWW[9], WPWW[9], WWPW[9];
+  mm3(Wm, P, WP);
+  mm3(P, Wm, PW);
+  mm3(WP, Wm, WPW);
+  mm3(Wm, WP, WWP);
+  mm3(PW, Wm, PWW);
+  mm3(WPW, Wm, WPWW);
+  mm3(Wm, WPW, WWPW);
+  double Q[9], Jw[9];
+  for (int k = 0; k < 9; ++k) {
+    Q[k] = 0.5 * P[k] + c1 * (WP[k] + PW[k] + WPW[k]) + c2 * (WWP[k] + PWW[k] - 3.0 * WPW[k]) +
+           c3 * (WPWW[k] + WWPW[k]);
+    Jw[k] = ((k % 4) == 0 ? 1.0 : 0.0) + B * Wm[k] + C * W2[k];
+  }
+  for (int k = 0; k < 36; ++k) J[k] = 0.0;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      J[6 * r + c] = Jw[3 * r + c];
+      J[6 * r + 3 + c] = Q[3 * r + c];
+      J[6 * (3 + r) + 3 + c] = Jw[3 * r + c];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Optimisation loop (Algorithm 2 with the pose-only reading):          */
+/* lambda anneal (Algorithm 3), gradient, tangent-space Adam, Exp.      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  double lambda0, lambda1;
+  int lambda_steps;
+  double delta, eps_z;
+  int norm_mode;
+  double lr_rot, lr_trans, beta1, beta2, eps;
+} oracle_opt;
+
+/* lambda_s: linear from lambda0 to lambda1 over lambda_steps, then held. */
+double oracle_lambda(const oracle_opt* o, int64_t s) {
+  double f = o->lambda_steps > 0 ? (double)s / o->lambda_steps : 1.0;
+  if (f > 1.0) f = 1.0;
+  return o->lambda0 + (o->lambda1 - o->lambda0) * f;
+}
+
+/*
+ * Run n_steps optimisation steps from step index `step0`.  T (n x 12) is
+ * updated in place; m, v (n x 6) are the Adam moments (in/out); loss_hist
+ * (n_steps, may be NULL) receives the loss evaluated before each update.
+ */
+int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, const oracle_opt* o,
+                    int64_t step0, int n_steps, double* m, double* v, double* loss_hist) {
+  int n = S->n_views;
+  double* G = (double*)malloc(sizeof(double) * 6 * n);
+  if (!G) return ORACLE_ENOMEM;
+  oracle_params prm;
+  prm.delta = o->delta;
+  prm.eps_z = o->eps_z;
+  prm.norm_mode = o->norm_mode;
+  prm.near_margin = 0.0;
+  for (int it = 0; it < n_steps; ++it) {
+    int64_t s = step0 + it;
+    prm.lambda = oracle_lambda(o, s);
+    double L;
+    int rc = oracle_loss_grad(S, T, &prm, &L, G, NULL, NULL, NULL);
+    if (rc) { free(G); return rc; }
+    if (loss_hist) loss_hist[it] = L;
+    double bc1 = 1.0 - pow(o->beta1, (double)(s + 1));
+    double bc2 = 1.0 - pow(o->beta2, (double)(s + 1));
+    for (int i = 0; i < n; ++i) {
+      if (fixed && fixed[i]) continue;
+      double delta[6];
+      for (int k = 0; k < 6; ++k) {
+        double g = G[6 * i + k];
+        m[6 * i + k] = o->beta1 * m[6 * i + k] + (1.0 - o->beta1) * g;
+        v[6 * i + k] = o->beta2 * v[6 * i + k] + (1.0 - o->beta2) * g * g;
+        double mh = m[6 * i + k] / bc1, vh = v[6 * i + k] / bc2;
+        double lr = k < 3 ? o->lr_trans : o->lr_rot;
+        delta[k] = -lr * mh / (sqrt(vh) + o->eps);
+      }
+      double E[12], Tn[12];
+      oracle_se3_exp(delta, E);
+      /* T <- Exp(-Delta) T */
+      for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 4; ++c) {
+          double acc = c == 3 ? E[4 * r + 3] : 0.0;
+          for (int k = 0; k < 3; ++k) acc += E[4 * r + k] * T[12 * i + 4 * k + c];
+          Tn[4 * r + c] = acc;
+        }
+      }
+      memcpy(T + 12 * i, Tn, sizeof(Tn));
+    }
+  }
+  free(G);
+  return ORACLE_OK;
+}
