@@ -1,0 +1,235 @@
+/*
+ * epo.h -- C ABI of the GB300 (sm_103a) edge-alignment library.
+ *
+ * The library evaluates EPO's multi-view edge-alignment objective (Section 3,
+ * "Edge Reprojection Loss", Eqs. 6-8) and its 6-DoF gradient with respect to
+ * every camera pose, and runs the pose-only optimisation loop of Algorithm 2
+ * (with the clamp anneal and batched residuals of Algorithm 3) entirely on
+ * one GPU.  Everything here is plain C: pointers, sizes and status codes; no
+ * exception crosses this boundary and the library never exits or traps.
+ *
+ * Conventions used by every entry point
+ *   - Pose T_i = [R_i | t_i] maps world -> camera i (the extrinsic P_i of
+ *     Section 3, Eq. 1), row-major 3x4, 12 doubles per view.
+ *   - Pixel centres at integer coordinates; depth is z-depth; K_i given as
+ *     (fx, fy, cx, cy).
+ *   - Edge record of view i: (u, v, z) = pixel of an edge in E_i and its
+ *     predicted depth Z_i(u, v).  EPO_F32 records are 16 bytes
+ *     {float u, float v, float z, float 0}; EPO_F16 records are 8 bytes
+ *     {uint16 u, uint16 v, half z, uint16 0}.
+ *   - Map of view j: its distance transform field DTF_j (Section 3), H rows
+ *     of W values, row-major, dense; EPO_F32 (float) or EPO_BF16.
+ *   - Pairs: directed (i -> j) index pairs into the view array; the loss is
+ *     L = (2/P) sum_p l_p with l_p the per-direction mean of Eq. 7, which is
+ *     Eq. 6 when every undirected pair is listed in both directions.
+ *   - Gradients are with respect to a left perturbation T <- Exp(xi) T,
+ *     xi = (upsilon, omega) (translation first), 6 doubles per view.
+ *   - A projected sample is valid iff its camera-j depth exceeds eps_z and
+ *     it lands in [0, W-1] x [0, H-1]; invalid samples do not count in the
+ *     per-direction mean (Algorithm 3, sum(rho) / sum(valid)).
+ *
+ * Streams and ownership
+ *   - Every call is ordered on the CUDA stream given at creation (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Calls with host outputs synchronise that stream before returning;
+ *     calls suffixed _dev take device pointers and do not synchronise.
+ *   - A scene handle is not thread-safe: one host thread at a time.
+ *   - epo_create_* copy every input into library-owned device memory; the
+ *     caller may free its buffers as soon as the call returns.
+ */
+#ifndef EPO_H
+#define EPO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPO_ABI_VERSION 1
+
+typedef enum {
+  EPO_OK = 0,
+  EPO_ERR_INVALID_ARG = 1, /* bad sizes, indices, pointers, dtypes or non-finite maps */
+  EPO_ERR_CUDA = 2,        /* a CUDA runtime call failed; see epo_last_error */
+  EPO_ERR_OOM = 3,         /* device allocation failed */
+  EPO_ERR_NUMERIC = 4,     /* non-finite loss or gradient; the pose update was refused */
+  EPO_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
+  EPO_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} epo_status;
+
+enum { EPO_F32 = 0, EPO_F16 = 1, EPO_BF16 = 2 };
+/* Per-direction normaliser: sum(valid) (Algorithm 3) or |E_i| (Eq. 7). */
+enum { EPO_NORM_VALID = 0, EPO_NORM_ALL = 1 };
+/* How the kernels read the 2x2 map footprint: plain loads or texture gather. */
+enum { EPO_GATHER_AUTO = 0, EPO_GATHER_LDG = 1, EPO_GATHER_TEX = 2 };
+
+typedef struct epo_scene* epo_scene_t;
+
+/* One view: intrinsics K_i, its edge records (E_i with depth Z_i) and its
+ * distance transform field DTF_i (Eq. 1 augmented as in Section 3). */
+typedef struct {
+  int32_t W, H;              /* map size; both >= 2 */
+  double fx, fy, cx, cy;     /* pinhole intrinsics, fx, fy > 0 */
+  const void* records;       /* n_records records of the scene's record dtype */
+  int64_t n_records;         /* >= 0 */
+  const void* map;           /* W*H values of the scene's map dtype, finite, >= 0 */
+} epo_view_desc;
+
+/* One scene: the views, the directed viewgraph E (Section 3, "Viewgraph
+ * Estimation"; here supplied by the caller) and the gauge mask. */
+typedef struct {
+  int32_t n_views;           /* >= 1 */
+  const epo_view_desc* views;
+  int32_t n_pairs;           /* >= 1 */
+  const int32_t* pairs;      /* 2*n_pairs ints: (i, j) per directed pair, i != j allowed */
+  const uint8_t* fixed;      /* n_views bytes, 1 = pose frozen by epo_step; NULL = none */
+  int32_t record_dtype;      /* EPO_F32 | EPO_F16 */
+  int32_t map_dtype;         /* EPO_F32 | EPO_BF16 */
+  int32_t pointers_on_device;/* 0: records/map are host pointers, 1: device pointers */
+} epo_scene_desc;
+
+/* Hyper-parameters (Section 3 "Implementation Details", Algorithm 3). */
+typedef struct {
+  double huber_delta;        /* Huber threshold (paper silent; default 1 px) */
+  double lambda0, lambda1;   /* clamp anneal lambda0 -> lambda1 (Algorithm 3: 10 -> 6) */
+  int32_t lambda_steps;      /* over this many steps, linear, then held (default 1000) */
+  double eps_z;              /* minimum camera-j depth of a valid sample (default 1e-6) */
+  int32_t norm_mode;         /* EPO_NORM_VALID | EPO_NORM_ALL */
+  double lr_rot, lr_trans;   /* Adam step sizes for omega and upsilon */
+  double beta1, beta2, adam_eps; /* Adam moments (Section 3: 0.9, 0.999) */
+  int32_t autotune;          /* 1: pick the kernel schedule by timing on first use */
+  int32_t gather;            /* EPO_GATHER_* (AUTO = LDG unless autotuned) */
+  int32_t block_threads;     /* 0 = default (256); else 64..1024, multiple of 32 */
+  int32_t records_per_thread;/* 0 = default (4); 2, 4 or 8 */
+  int32_t grid_blocks;       /* 0 = default (persistent: SMs x resident blocks) */
+  int32_t timing;            /* 1: bracket the edge kernel with CUDA events (epo_kernel_time) */
+} epo_options;
+
+/* Per-scene facts, filled by epo_scene_info. */
+typedef struct {
+  int32_t n_scenes, n_views, n_pairs;
+  int64_t n_records;         /* records kept on the device (all scenes) */
+  int64_t n_dropped;         /* records dropped at creation (z <= 0 or non-finite) */
+  int64_t evals_per_step;    /* sum over pairs of |E_i| : edge-pixel x pair evaluations */
+  int64_t device_bytes;      /* library-owned device memory */
+  int64_t record_bytes, map_bytes;
+  int32_t n_tiles;           /* work items of the persistent kernels */
+  int32_t gather, block_threads, records_per_thread, grid_blocks; /* schedule in use */
+} epo_scene_info;
+
+/* Defaults: delta 1, lambda 10 -> 6 over 1000 steps, eps_z 1e-6, NORM_VALID,
+ * lr_rot 2e-3, lr_trans 2e-2, beta (0.9, 0.999), adam_eps 1e-12, no autotune. */
+void epo_default_options(epo_options* opts);
+
+int32_t epo_abi_version(void);
+
+/* Build one scene (Algorithm 1's products: E_i, DTF_i, the viewgraph).
+ * Copies everything to the device.  Records with z <= 0 or non-finite are
+ * dropped and counted; maps with a non-finite or negative value, W or H < 2,
+ * pair indices out of range or unknown dtypes give EPO_ERR_INVALID_ARG.
+ * Poses start at identity; set them with epo_set_poses. */
+epo_status epo_create_scene(const epo_scene_desc* desc, const epo_options* opts, void* cuda_stream,
+                            epo_scene_t* out);
+
+/* Several independent scenes of uneven sizes in one handle: one persistent
+ * launch evaluates all of them (the batching of Algorithm 3 extended across
+ * scenes).  Views and poses of scene s follow those of scene s-1; the loss
+ * is reported per scene. */
+epo_status epo_create_batch(int32_t n_scenes, const epo_scene_desc* descs, const epo_options* opts,
+                            void* cuda_stream, epo_scene_t* out);
+
+void epo_destroy_scene(epo_scene_t scene);
+
+/* Detail of the last failure on this handle (or of the last failed create
+ * when scene is NULL).  Valid until the next call on the handle. */
+const char* epo_last_error(epo_scene_t scene);
+
+epo_status epo_scene_info_get(epo_scene_t scene, epo_scene_info* info);
+
+/* Poses, n_views x 12 doubles (host).  set: synchronous copy; get: syncs. */
+epo_status epo_set_poses(epo_scene_t scene, const double* T);
+epo_status epo_get_poses(epo_scene_t scene, double* T);
+/* Same with device pointers, stream-ordered. */
+epo_status epo_set_poses_dev(epo_scene_t scene, const double* T_dev);
+epo_status epo_get_poses_dev(epo_scene_t scene, double* T_dev);
+
+/* Optimiser state for checkpoint / resume: the step counter (drives the
+ * clamp anneal and Adam's bias correction) and Adam's moments (n_views x 6
+ * each, host).  Resuming = set poses + set state. */
+epo_status epo_get_state(epo_scene_t scene, int64_t* step, double* m, double* v);
+epo_status epo_set_state(epo_scene_t scene, int64_t step, const double* m, const double* v);
+
+/* Loss (Eq. 6, one value per scene) and gradient (n_views x 6) at the
+ * current poses, with lambda from the anneal at the current step.  grad may
+ * be NULL.  Host outputs; synchronises. */
+epo_status epo_loss_and_grad(epo_scene_t scene, double* loss, double* grad);
+/* Device outputs: loss_dev n_scenes doubles, grad_dev n_views x 6 (may be NULL). */
+epo_status epo_loss_and_grad_dev(epo_scene_t scene, double* loss_dev, double* grad_dev);
+
+/* Per-pair accumulators of the last evaluation, n_pairs x 8 doubles (host):
+ * sum rho, n_valid, sum dRho/dY (3, camera-j frame), sum Y x dRho/dY (3).
+ * The last six hold the gradient pass's sums; after a forward-only pass
+ * they are zero. */
+epo_status epo_pair_stats(epo_scene_t scene, double* stats);
+
+/* Forward / adjoint pair behind an autograd function of the twists xi
+ * (n_views x 6, device): poses T_i(xi) = Exp(xi_i) T_i.  forward writes the
+ * per-scene loss; backward takes dL_out/dloss per scene (device, n_scenes)
+ * and writes d(out)/d(xi) = J_l(xi)^T g (J_l the SE(3) left Jacobian, g the
+ * left-perturbation gradient at T(xi)), recomputing every projection instead
+ * of storing per-sample Jacobians (the analytical backward of Algorithm 2's
+ * fused kernels).  xi_dev may be NULL (= zero).  backward must follow a
+ * forward at the same xi (it reuses the forward's n_valid per pair). */
+epo_status epo_forward_dev(epo_scene_t scene, const double* xi_dev, double* loss_dev);
+epo_status epo_backward_dev(epo_scene_t scene, const double* xi_dev, const double* dloss_dev,
+                            double* grad_xi_dev);
+
+/* n_steps optimisation steps (Algorithm 2, pose-only reading): clamp anneal,
+ * loss + gradient, tangent-space Adam, T_i <- Exp(-Delta_i) T_i for every
+ * view not fixed.  Each step is one replay of a CUDA graph; lambda, the step
+ * counter and Adam's state live on the device.  epo_step synchronises at the
+ * end and returns EPO_ERR_NUMERIC if a step saw a non-finite loss or
+ * gradient (that step and the later ones left the poses unchanged);
+ * epo_step_async does not synchronise (check with epo_check). */
+epo_status epo_step(epo_scene_t scene, int32_t n_steps);
+epo_status epo_step_async(epo_scene_t scene, int32_t n_steps);
+/* The per-step form without the graph: the same kernels launched one by
+ * one from the host every step (the plain form the graph is compared to). */
+epo_status epo_step_plain(epo_scene_t scene, int32_t n_steps);
+/* Synchronise and report a pending numeric flag (and clear it). */
+epo_status epo_check(epo_scene_t scene);
+
+/* Loss per scene (host, n_scenes doubles) computed by the most recent
+ * evaluation or step (a step evaluates before it updates).  Synchronises. */
+epo_status epo_last_loss(epo_scene_t scene, double* loss);
+
+/* Device time in milliseconds of the edge kernel (steps a2-a7) in the most
+ * recent evaluation or step; needs options.timing = 1.  Synchronises. */
+epo_status epo_kernel_time(epo_scene_t scene, float* ms);
+
+/* Evaluate only a subset of the pairs from now on (the stochastic viewgraph
+ * sub-sampling of Algorithm 3 / Appendix A.3; the draw is the caller's).
+ * pair_ids: n distinct indices (host); n = 0 restores all pairs.  The loss
+ * then averages over the active pairs of each scene. */
+epo_status epo_set_pair_subset(epo_scene_t scene, int32_t n, const int32_t* pair_ids);
+
+/* Time the kernel schedules on the current poses and keep the fastest
+ * (block size, records per thread, gather path). */
+epo_status epo_autotune(epo_scene_t scene);
+
+/* Distance transform field (Algorithm 1, ComputeDistanceFields): exact
+ * Euclidean distance from every pixel to the nearest nonzero pixel of the
+ * edge mask, W + H everywhere when the mask is empty.  edges_dev: W*H bytes,
+ * map_dev: W*H floats (both device, row-major); map_dev also serves as the
+ * intermediate.  Stream-ordered. */
+epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, float* map_dev,
+                              void* cuda_stream);
+/* Round n floats to bfloat16 (round to nearest even), device buffers. */
+epo_status epo_round_bf16(const float* src_dev, uint16_t* dst_dev, int64_t n, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPO_H */

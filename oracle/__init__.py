@@ -73,7 +73,7 @@ def _load():
         lib.oracle_edt_brute.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
         lib.oracle_robust.argtypes = [ctypes.c_double] * 3 + [P, P]
         lib.oracle_robust.restype = None
-        lib.oracle_loss_grad.argtypes = [P, P, P, P, P, P, P, P]
+        lib.oracle_loss_grad.argtypes = [P, P, P, P, P, P, P, P, P, P]
         lib.oracle_se3_exp.argtypes = [P, P]
         lib.oracle_se3_exp.restype = None
         lib.oracle_se3_log.argtypes = [P, P]
@@ -170,7 +170,8 @@ class OracleScene:
 
     def loss_grad(self, T: np.ndarray, lam: float, delta: float = 1.0, eps_z: float = 1e-6,
                   norm_mode: int = NORM_VALID, near_margin: float = 1e-3):
-        """Returns dict(loss, grad (n,6), pair_stats (P,8), pair_near (P,), pair_loss (P,))."""
+        """Returns dict(loss, grad (n,6), pair_stats (P,8), pair_near (P,), pair_loss (P,),
+        pair_abs (P,6), pair_maxterm (P,))."""
         T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12)
         prm = _Params(lam, delta, eps_z, norm_mode, near_margin)
         loss = np.zeros(1)
@@ -179,12 +180,15 @@ class OracleScene:
         st = np.zeros((P, 8))
         near = np.zeros(P, dtype=np.int64)
         pl = np.zeros(P)
+        ab = np.zeros((P, 6))
+        mt = np.zeros(P)
         rc = _load().oracle_loss_grad(ctypes.byref(self._s), _p(T), ctypes.byref(prm), _p(loss), _p(grad),
-                                      _p(st), _p(near), _p(pl))
+                                      _p(st), _p(near), _p(pl), _p(ab), _p(mt))
         if rc:
             raise ValueError(f"oracle_loss_grad failed ({rc})")
         return dict(loss=float(loss[0]), grad=grad, pair_stats=st[:self.n_pairs],
-                    pair_near=near[:self.n_pairs], pair_loss=pl[:self.n_pairs])
+                    pair_near=near[:self.n_pairs], pair_loss=pl[:self.n_pairs], pair_abs=ab[:self.n_pairs],
+                    pair_maxterm=mt[:self.n_pairs])
 
     def optimize(self, T: np.ndarray, fixed: np.ndarray, n_steps: int, *, lambda0=10.0, lambda1=6.0,
                  lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID, lr_rot=1e-3,

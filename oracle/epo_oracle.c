@@ -200,7 +200,7 @@ static void unproject(const double* K, const double* T, const double* rec, doubl
  */
 static void pair_terms(const oracle_scene* S, const double* T, const double* Xw_all,
                        const oracle_params* prm, int p, double stats[8], double gi[6],
-                       double gj[6], int64_t* near) {
+                       double gj[6], int64_t* near, double absum[6], double* maxterm) {
   int i = S->pairs[2 * p], j = S->pairs[2 * p + 1];
   const double* Ti = T + 12 * i;
   const double* Tj = T + 12 * j;
@@ -210,8 +210,9 @@ static void pair_terms(const oracle_scene* S, const double* T, const double* Xw_
   const double* map = S->map + S->map_off[j];
   double fx = Kj[0], fy = Kj[1], cx = Kj[2], cy = Kj[3];
   for (int k = 0; k < 8; ++k) stats[k] = 0.0;
-  for (int k = 0; k < 6; ++k) gi[k] = gj[k] = 0.0;
+  for (int k = 0; k < 6; ++k) gi[k] = gj[k] = absum[k] = 0.0;
   *near = 0;
+  *maxterm = 0.0;
   for (int64_t r = S->rec_off[i]; r < S->rec_off[i + 1]; ++r) {
     const double* Xw = Xw_all + 3 * r;
     double Y[3];
@@ -251,9 +252,13 @@ static void pair_terms(const oracle_scene* S, const double* T, const double* Xw_
     gY[2] = -drho * (dd_du * fx * Y[0] + dd_dv * fy * Y[1]) / (z * z);
     double c[3] = {Y[1] * gY[2] - Y[2] * gY[1], Y[2] * gY[0] - Y[0] * gY[2],
                    Y[0] * gY[1] - Y[1] * gY[0]};
+    double tn = sqrt(gY[0] * gY[0] + gY[1] * gY[1] + gY[2] * gY[2] + c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    if (tn > *maxterm) *maxterm = tn;
     for (int k = 0; k < 3; ++k) {
       stats[2 + k] += gY[k];
       stats[5 + k] += c[k];
+      absum[k] += fabs(gY[k]);
+      absum[3 + k] += fabs(c[k]);
       gj[k] += gY[k];
       gj[3 + k] += c[k];
     }
@@ -283,11 +288,14 @@ static void pair_terms(const oracle_scene* S, const double* T, const double* Xw_
 /*
  * Objective and gradient (Eqs. 6-8).  T: n_views x 12.  Outputs:
  *   loss (scalar), grad (n_views x 6, may be NULL), pair_stats (P x 8, may be
- *   NULL), pair_near (P, may be NULL), pair_loss (P, may be NULL).
+ *   NULL), pair_near (P, may be NULL), pair_loss (P, may be NULL), pair_abs (P x 6,
+ *   may be NULL: sum over valid samples of |dRho/dY_k| and |(Y x dRho/dY)_k|, the scale
+ *   of the cancellation inside stats[2..7]), pair_maxterm (P, may be NULL: largest
+ *   norm of one valid sample's (dRho/dY, Y x dRho/dY)).
  */
 int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params* prm,
                      double* loss, double* grad, double* pair_stats, int64_t* pair_near,
-                     double* pair_loss) {
+                     double* pair_loss, double* pair_abs, double* pair_maxterm) {
   if (!S || !T || !prm || !loss) return ORACLE_EINVAL;
   int n = S->n_views, P = S->n_pairs;
   for (int p = 0; p < P; ++p) {
@@ -300,8 +308,10 @@ int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params
   double* gi = (double*)malloc(sizeof(double) * 6 * (P > 0 ? P : 1));
   double* gj = (double*)malloc(sizeof(double) * 6 * (P > 0 ? P : 1));
   int64_t* nr = (int64_t*)malloc(sizeof(int64_t) * (P > 0 ? P : 1));
-  if (!Xw || !st || !gi || !gj || !nr) {
-    free(Xw); free(st); free(gi); free(gj); free(nr);
+  double* ab = (double*)malloc(sizeof(double) * 6 * (P > 0 ? P : 1));
+  double* mt = (double*)malloc(sizeof(double) * (P > 0 ? P : 1));
+  if (!Xw || !st || !gi || !gj || !nr || !ab || !mt) {
+    free(Xw); free(st); free(gi); free(gj); free(nr); free(ab); free(mt);
     return ORACLE_ENOMEM;
   }
   /* UnprojectEdgesTo3D: once per view (Algorithm 2) */
@@ -312,7 +322,8 @@ int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params
     }
   /* ProjectSampleHuber for every directed pair */
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int p = 0; p < P; ++p) pair_terms(S, T, Xw, prm, p, st + 8 * p, gi + 6 * p, gj + 6 * p, nr + p);
+  for (int p = 0; p < P; ++p)
+    pair_terms(S, T, Xw, prm, p, st + 8 * p, gi + 6 * p, gj + 6 * p, nr + p, ab + 6 * p, mt + p);
   /* per-direction means and the pair average, in fixed order */
   double L = 0.0;
   if (grad)
@@ -332,9 +343,12 @@ int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params
     if (pair_stats)
       for (int k = 0; k < 8; ++k) pair_stats[8 * p + k] = st[8 * p + k];
     if (pair_near) pair_near[p] = nr[p];
+    if (pair_abs)
+      for (int k = 0; k < 6; ++k) pair_abs[6 * p + k] = ab[6 * p + k];
+    if (pair_maxterm) pair_maxterm[p] = mt[p];
   }
   *loss = P > 0 ? (2.0 / P) * L : 0.0;
-  free(Xw); free(st); free(gi); free(gj); free(nr);
+  free(Xw); free(st); free(gi); free(gj); free(nr); free(ab); free(mt);
   return ORACLE_OK;
 }
 
@@ -529,7 +543,7 @@ int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, cons
     int64_t s = step0 + it;
     prm.lambda = oracle_lambda(o, s);
     double L;
-    int rc = oracle_loss_grad(S, T, &prm, &L, G, NULL, NULL, NULL);
+    int rc = oracle_loss_grad(S, T, &prm, &L, G, NULL, NULL, NULL, NULL, NULL);
     if (rc) { free(G); return rc; }
     if (loss_hist) loss_hist[it] = L;
     double bc1 = 1.0 - pow(o->beta1, (double)(s + 1));

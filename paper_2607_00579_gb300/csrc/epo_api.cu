@@ -1,0 +1,927 @@
+// C ABI of the edge-alignment library: scene construction (device layout), evaluation,
+// the graph-captured optimisation step, the autograd forward/adjoint pair, the autotuner.
+// Declarations and argument conventions: include/epo.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/epo.h"
+#include "epo_internal.cuh"
+
+using namespace epo;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// IEEE binary16 -> float on the host (used to validate FP16-depth records).
+float half_bits_to_float(uint16_t h) {
+  const uint32_t sign = (uint32_t)(h >> 15) << 31;
+  const uint32_t exp = (h >> 10) & 0x1f;
+  const uint32_t man = h & 0x3ff;
+  float f;
+  if (exp == 0) {
+    f = ldexpf((float)man, -24);
+  } else if (exp == 31) {
+    f = man ? NAN : INFINITY;
+  } else {
+    f = ldexpf((float)(man | 0x400), (int)exp - 25);
+  }
+  uint32_t bits;
+  memcpy(&bits, &f, 4);
+  bits |= sign;
+  memcpy(&f, &bits, 4);
+  return f;
+}
+
+}  // namespace
+
+struct epo_scene {
+  // configuration
+  epo_options opt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int rec_dtype = 0;  // 0 f32, 1 f16
+  int map_dtype = 0;  // 0 f32, 1 bf16
+  int n_scenes = 0, n_views = 0, n_pairs = 0;
+  int64_t n_records = 0, n_dropped = 0, evals = 0;
+  int sm_count = 0;
+  // schedule
+  int gather = GATHER_LDG, block = 256, rpt = 4, grid = 0;
+  bool tuned = false;
+  // host tables
+  std::vector<ViewDev> views;
+  std::vector<int32_t> pair_src, pair_dst, pair_scene, scene_pair_off, scene_active;
+  std::vector<int32_t> src_pair_off, src_pair_ids;
+  std::vector<uint8_t> active;
+  // device buffers
+  std::vector<DevBuf> bufs;
+  void* d_rec = nullptr;
+  void* d_map = nullptr;
+  int64_t map_elems = 0;
+  ViewDev* d_views = nullptr;
+  TileDev* d_tiles = nullptr;
+  int32_t n_tiles = 0;
+  int tiles_for = -1;  // tile size the table was built for
+  int32_t *d_src_pair_off = nullptr, *d_src_pair_ids = nullptr, *d_pair_src = nullptr,
+          *d_pair_dst = nullptr, *d_pair_scene = nullptr, *d_scene_pair_off = nullptr,
+          *d_scene_active = nullptr, *d_pose_pair_off = nullptr, *d_pose_pair_ref = nullptr;
+  uint8_t *d_active = nullptr, *d_fixed = nullptr;
+  unsigned long long* d_tex = nullptr;
+  std::vector<cudaTextureObject_t> tex;
+  std::vector<cudaArray_t> arrays;
+  PairParam* d_pp = nullptr;
+  double *d_pair_acc = nullptr, *d_pair_loss = nullptr, *d_contrib = nullptr, *d_grad = nullptr,
+         *d_loss = nullptr, *d_m = nullptr, *d_v = nullptr, *d_lambda = nullptr, *d_T = nullptr,
+         *d_T_eval = nullptr, *d_grad_tmp = nullptr;
+  int64_t* d_step = nullptr;
+  int32_t* d_flag = nullptr;
+  unsigned int* d_done = nullptr;
+  int32_t* h_flag = nullptr;  // pinned
+  int64_t device_bytes = 0;
+  // edge-kernel timing events (options.timing)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ev_recorded = false;
+  // graph of one optimisation step
+  cudaGraphExec_t graph = nullptr;
+  bool graph_dirty = true;
+  std::string err;
+};
+
+namespace {
+
+epo_status fail(epo_scene* s, epo_status code, const std::string& msg) {
+  if (s)
+    s->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+epo_status cuda_fail(epo_scene* s, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(s, e == cudaErrorMemoryAllocation ? EPO_ERR_OOM : EPO_ERR_CUDA, m);
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(S, e_, #call); \
+  } while (0)
+
+template <typename T>
+epo_status dalloc(epo_scene* S, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_fail(S, e, "cudaMalloc");
+  S->bufs.push_back({q, bytes});
+  S->device_bytes += (int64_t)bytes;
+  *p = reinterpret_cast<T*>(q);
+  return EPO_OK;
+}
+
+#define ALLOC(ptr, count)                       \
+  do {                                          \
+    epo_status st_ = dalloc(S, &(ptr), (count)); \
+    if (st_ != EPO_OK) return st_;              \
+  } while (0)
+
+StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_views = S->n_views;
+  a.n_pairs = S->n_pairs;
+  a.n_scenes = S->n_scenes;
+  a.pair_src = S->d_pair_src;
+  a.pair_dst = S->d_pair_dst;
+  a.pair_scene = S->d_pair_scene;
+  a.pair_active = S->d_active;
+  a.scene_pair_off = S->d_scene_pair_off;
+  a.scene_active_pairs = S->d_scene_active;
+  a.pose_pair_off = S->d_pose_pair_off;
+  a.pose_pair_ref = S->d_pose_pair_ref;
+  a.views = S->d_views;
+  a.fixed = S->d_fixed;
+  a.T = T_eval;
+  a.T_store = S->d_T;
+  a.pp = S->d_pp;
+  a.pair_acc = S->d_pair_acc;
+  a.pair_loss = S->d_pair_loss;
+  a.contrib = S->d_contrib;
+  a.grad = S->d_grad;
+  a.loss = S->d_loss;
+  a.m = S->d_m;
+  a.v = S->d_v;
+  a.step = S->d_step;
+  a.lambda = S->d_lambda;
+  a.flag = S->d_flag;
+  a.done = S->d_done;
+  a.gscale = gscale;
+  a.lambda0 = S->opt.lambda0;
+  a.lambda1 = S->opt.lambda1;
+  a.lambda_steps = S->opt.lambda_steps;
+  a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
+  a.lr_rot = S->opt.lr_rot;
+  a.lr_trans = S->opt.lr_trans;
+  a.beta1 = S->opt.beta1;
+  a.beta2 = S->opt.beta2;
+  a.adam_eps = S->opt.adam_eps;
+  return a;
+}
+
+epo_status build_tiles(epo_scene* S, int tile) {
+  if (S->tiles_for == tile) return EPO_OK;
+  std::vector<TileDev> t;
+  for (int v = 0; v < S->n_views; ++v) {
+    const ViewDev& vd = S->views[v];
+    if (vd.n_rec == 0 || S->src_pair_off[v + 1] == S->src_pair_off[v]) continue;
+    for (int64_t b = 0; b < vd.n_rec; b += tile) {
+      TileDev td;
+      td.view = v;
+      td.begin = vd.rec_begin + b;
+      td.n = (int32_t)std::min<int64_t>(tile, vd.n_rec - b);
+      t.push_back(td);
+    }
+  }
+  if (S->d_tiles) {
+    cudaFree(S->d_tiles);
+    for (auto& b : S->bufs)
+      if (b.p == S->d_tiles) {
+        S->device_bytes -= (int64_t)b.n;
+        b.p = nullptr;
+      }
+    S->d_tiles = nullptr;
+  }
+  ALLOC(S->d_tiles, t.size());
+  if (!t.empty()) CK(cudaMemcpy(S->d_tiles, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+  S->n_tiles = (int32_t)t.size();
+  S->tiles_for = tile;
+  S->graph_dirty = true;
+  return EPO_OK;
+}
+
+EdgeArgs edge_args(epo_scene* S) {
+  EdgeArgs a;
+  memset(&a, 0, sizeof(a));
+  a.rec = S->d_rec;
+  a.map = S->d_map;
+  a.views = S->d_views;
+  a.tiles = S->d_tiles;
+  a.n_tiles = S->n_tiles;
+  a.src_pair_off = S->d_src_pair_off;
+  a.src_pair_ids = S->d_src_pair_ids;
+  a.pair_dst = S->d_pair_dst;
+  a.pp = S->d_pp;
+  a.pair_active = S->d_active;
+  a.tex = S->d_tex;
+  a.pair_acc = S->d_pair_acc;
+  a.lambda = S->d_lambda;
+  a.delta = (float)S->opt.huber_delta;
+  a.eps_z = (float)S->opt.eps_z;
+  return a;
+}
+
+int grid_for(epo_scene* S, int gather, int rpt, int block) {
+  if (S->opt.grid_blocks > 0) return S->opt.grid_blocks;
+  // resident blocks per SM from the register/shared budget (<= 2048 threads per SM)
+  int per_sm = std::max(1, 2048 / block);
+  if (rpt >= 8) per_sm = std::max(1, per_sm / 2);
+  (void)gather;
+  int g = S->sm_count * per_sm;
+  return std::max(1, std::min(g, std::max(S->n_tiles, 1)));
+}
+
+epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, cudaStream_t s) {
+  epo_status st = build_tiles(S, block * rpt);
+  if (st != EPO_OK) return st;
+  EdgeArgs ea = edge_args(S);
+  int grid = grid_for(S, gather, rpt, block);
+  // inside a stream capture the timing events become event-record nodes of the graph
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (S->ev0) CK(cudaStreamIsCapturing(s, &cap));
+  const unsigned int evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (S->ev0) CK(cudaEventRecordWithFlags(S->ev0, s, evf));
+  CK(launch_edge(ea, mode, S->rec_dtype, S->map_dtype, gather, rpt, block, grid, s));
+  if (S->ev1) {
+    CK(cudaEventRecordWithFlags(S->ev1, s, evf));
+    S->ev_recorded = true;
+  }
+  return EPO_OK;
+}
+
+// One evaluation with gradient (a1 .. a8) on stream s.
+epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval) {
+  StepArgs a = step_args(S, T_eval, nullptr);
+  CK(launch_pair_setup(a, MODE_FUSED, s));
+  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, s);
+  if (st != EPO_OK) return st;
+  CK(launch_finalize(a, 1, s));
+  return EPO_OK;
+}
+
+epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
+  epo_status st = enqueue_loss_grad(S, s, S->d_T);
+  if (st != EPO_OK) return st;
+  StepArgs a = step_args(S, S->d_T, nullptr);
+  CK(launch_retract(a, s));
+  return EPO_OK;
+}
+
+epo_status ensure_graph(epo_scene* S) {
+  // build the tile table outside capture (it allocates)
+  epo_status st = build_tiles(S, S->block * S->rpt);
+  if (st != EPO_OK) return st;
+  if (!S->graph_dirty && S->graph) return EPO_OK;
+  if (S->graph) {
+    cudaGraphExecDestroy(S->graph);
+    S->graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+  st = enqueue_step(S, S->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
+  if (st != EPO_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(S, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&S->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(S, e, "cudaGraphInstantiate");
+  S->graph_dirty = false;
+  return EPO_OK;
+}
+
+epo_status maybe_autotune(epo_scene* S) {
+  if (S->opt.autotune && !S->tuned) return epo_autotune(S);
+  return EPO_OK;
+}
+
+epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_options* opts,
+                       void* cuda_stream, epo_scene_t* out, epo_scene* S) {
+  if (!descs || !out || n_scenes < 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "null descriptor or n_scenes < 1");
+  epo_default_options(&S->opt);
+  if (opts) S->opt = *opts;
+  const epo_options& o = S->opt;
+  if (!(o.huber_delta > 0) || !(o.eps_z >= 0) || o.lambda_steps < 0 || !(o.lambda0 > 0) || !(o.lambda1 > 0) ||
+      (o.norm_mode != EPO_NORM_VALID && o.norm_mode != EPO_NORM_ALL) || !(o.beta1 >= 0 && o.beta1 < 1) ||
+      !(o.beta2 >= 0 && o.beta2 < 1) || !(o.adam_eps >= 0))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid options");
+  if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "block_threads must be 64..512, a multiple of 32");
+  if (o.records_per_thread != 0 && o.records_per_thread != 2 && o.records_per_thread != 4 &&
+      o.records_per_thread != 8)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 2, 4 or 8");
+  if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
+  S->stream = (cudaStream_t)cuda_stream;
+  const int rec_dtype = descs[0].record_dtype, map_dtype = descs[0].map_dtype;
+  if (rec_dtype != EPO_F32 && rec_dtype != EPO_F16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown record dtype");
+  if (map_dtype != EPO_F32 && map_dtype != EPO_BF16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown map dtype");
+  S->rec_dtype = rec_dtype == EPO_F16 ? 1 : 0;
+  S->map_dtype = map_dtype == EPO_BF16 ? 1 : 0;
+  const size_t rec_size = S->rec_dtype ? 8 : 16;
+  const size_t map_size = S->map_dtype ? 2 : 4;
+  // ---- validate descriptors, count ----
+  int64_t nv = 0, np = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    const epo_scene_desc& d = descs[s];
+    if (d.record_dtype != rec_dtype || d.map_dtype != map_dtype)
+      return fail(nullptr, EPO_ERR_INVALID_ARG, "all scenes of a batch must share the dtypes");
+    if (d.n_views < 1 || !d.views) return fail(nullptr, EPO_ERR_INVALID_ARG, "scene without views");
+    if (d.n_pairs < 1 || !d.pairs) return fail(nullptr, EPO_ERR_INVALID_ARG, "scene without pairs");
+    for (int v = 0; v < d.n_views; ++v) {
+      const epo_view_desc& vd = d.views[v];
+      if (vd.W < 2 || vd.H < 2) return fail(nullptr, EPO_ERR_INVALID_ARG, "view with W or H < 2");
+      if (vd.W > 65535 || vd.H > 65535) return fail(nullptr, EPO_ERR_INVALID_ARG, "view larger than 65535");
+      if (!(vd.fx > 0) || !(vd.fy > 0) || !isfinite(vd.cx) || !isfinite(vd.cy) || !isfinite(vd.fx) || !isfinite(vd.fy))
+        return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid intrinsics");
+      if (vd.n_records < 0 || (vd.n_records > 0 && !vd.records))
+        return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid records");
+      if (!vd.map) return fail(nullptr, EPO_ERR_INVALID_ARG, "view without a map");
+    }
+    for (int p = 0; p < d.n_pairs; ++p) {
+      int i = d.pairs[2 * p], j = d.pairs[2 * p + 1];
+      if (i < 0 || i >= d.n_views || j < 0 || j >= d.n_views)
+        return fail(nullptr, EPO_ERR_INVALID_ARG, "pair index out of range");
+    }
+    nv += d.n_views;
+    np += d.n_pairs;
+  }
+  if (nv > (1 << 28) || np > (1 << 28)) return fail(nullptr, EPO_ERR_INVALID_ARG, "too many views or pairs");
+  S->n_scenes = n_scenes;
+  S->n_views = (int)nv;
+  S->n_pairs = (int)np;
+  // ---- device properties ----
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  // ---- records (host-side filtering) and host tables ----
+  std::vector<uint8_t> rec_host;
+  std::vector<uint8_t> tmp;
+  S->views.resize(nv);
+  std::vector<int32_t> pose_pair_cnt(nv, 0);
+  std::vector<uint8_t> fixed(nv, 0);
+  int64_t vbase = 0, map_off = 0, rec_off = 0;
+  const int64_t pitch_mult = 128 / (int64_t)map_size;           // 128-byte rows
+  const int64_t base_mult = 512 / (int64_t)map_size;            // 512-byte view starts
+  S->scene_pair_off.push_back(0);
+  for (int s = 0; s < n_scenes; ++s) {
+    const epo_scene_desc& d = descs[s];
+    for (int v = 0; v < d.n_views; ++v) {
+      const epo_view_desc& vd = d.views[v];
+      ViewDev& w = S->views[vbase + v];
+      w.fx = (float)vd.fx; w.fy = (float)vd.fy; w.cx = (float)vd.cx; w.cy = (float)vd.cy;
+      w.W = vd.W; w.H = vd.H;
+      w.pitch = (int32_t)round_up(vd.W, pitch_mult);
+      w.scene = s;
+      map_off = round_up(map_off, base_mult);
+      w.map_off = map_off;
+      map_off += (int64_t)w.pitch * vd.H;
+      w.rec_begin = rec_off;
+      w.pad_ = 0;
+      const uint8_t* src = (const uint8_t*)vd.records;
+      if (vd.n_records > 0 && d.pointers_on_device) {
+        tmp.resize((size_t)vd.n_records * rec_size);
+        e = cudaMemcpy(tmp.data(), vd.records, tmp.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMemcpy records D2H");
+        src = tmp.data();
+      }
+      int64_t kept = 0;
+      for (int64_t r = 0; r < vd.n_records; ++r) {
+        const uint8_t* q = src + (size_t)r * rec_size;
+        float z, u, vv;
+        if (S->rec_dtype == 0) {
+          float f4[4];
+          memcpy(f4, q, 16);
+          u = f4[0]; vv = f4[1]; z = f4[2];
+          if (!isfinite(u) || !isfinite(vv)) { ++S->n_dropped; continue; }
+        } else {
+          uint16_t h[4];
+          memcpy(h, q, 8);
+          z = half_bits_to_float(h[2]);
+          (void)u; (void)vv;
+        }
+        if (!(z > 0.f) || !isfinite(z)) { ++S->n_dropped; continue; }
+        rec_host.insert(rec_host.end(), q, q + rec_size);
+        ++kept;
+      }
+      if (kept > INT32_MAX) return fail(nullptr, EPO_ERR_INVALID_ARG, "too many records in one view");
+      w.n_rec = (int32_t)kept;
+      rec_off += kept;
+      if (d.fixed) fixed[vbase + v] = d.fixed[v] ? 1 : 0;
+    }
+    for (int p = 0; p < d.n_pairs; ++p) {
+      const int i = (int)vbase + d.pairs[2 * p], j = (int)vbase + d.pairs[2 * p + 1];
+      S->pair_src.push_back(i);
+      S->pair_dst.push_back(j);
+      S->pair_scene.push_back(s);
+      pose_pair_cnt[i]++;
+      pose_pair_cnt[j]++;
+    }
+    S->scene_pair_off.push_back((int32_t)S->pair_src.size());
+    S->scene_active.push_back(d.n_pairs);
+    vbase += d.n_views;
+  }
+  S->n_records = rec_off;
+  S->map_elems = std::max<int64_t>(map_off, 1);
+  S->active.assign(np, 1);
+  // pairs grouped by source view
+  S->src_pair_off.assign(nv + 1, 0);
+  for (int p = 0; p < np; ++p) S->src_pair_off[S->pair_src[p] + 1]++;
+  for (int v = 0; v < nv; ++v) S->src_pair_off[v + 1] += S->src_pair_off[v];
+  S->src_pair_ids.assign(np, 0);
+  {
+    std::vector<int32_t> fill(S->src_pair_off.begin(), S->src_pair_off.end() - 1);
+    for (int p = 0; p < np; ++p) S->src_pair_ids[fill[S->pair_src[p]]++] = p;
+  }
+  // per pose: (pair, role) in pair order -> deterministic gather
+  std::vector<int32_t> pose_off(nv + 1, 0), pose_ref(2 * np);
+  for (int v = 0; v < nv; ++v) pose_off[v + 1] = pose_off[v] + pose_pair_cnt[v];
+  {
+    std::vector<int32_t> fill(pose_off.begin(), pose_off.end() - 1);
+    for (int p = 0; p < np; ++p) {
+      pose_ref[fill[S->pair_dst[p]]++] = 2 * p + 0;
+      pose_ref[fill[S->pair_src[p]]++] = 2 * p + 1;
+    }
+  }
+  S->evals = 0;
+  for (int p = 0; p < np; ++p) S->evals += S->views[S->pair_src[p]].n_rec;
+  // ---- device allocations (CK / ALLOC report into the handle under construction) ----
+  {
+    e = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(S, e, "cudaStreamCreate");
+    ALLOC(*(uint8_t**)&S->d_rec, std::max<size_t>(rec_host.size(), 16));
+    {
+      uint8_t* raw = nullptr;
+      ALLOC(raw, (size_t)S->map_elems * map_size + 512);
+      S->d_map = (void*)(((uintptr_t)raw + 511) & ~(uintptr_t)511);
+    }
+    ALLOC(S->d_views, nv);
+    ALLOC(S->d_src_pair_off, nv + 1);
+    ALLOC(S->d_src_pair_ids, np);
+    ALLOC(S->d_pair_src, np);
+    ALLOC(S->d_pair_dst, np);
+    ALLOC(S->d_pair_scene, np);
+    ALLOC(S->d_scene_pair_off, n_scenes + 1);
+    ALLOC(S->d_scene_active, n_scenes);
+    ALLOC(S->d_pose_pair_off, nv + 1);
+    ALLOC(S->d_pose_pair_ref, 2 * np);
+    ALLOC(S->d_active, np);
+    ALLOC(S->d_fixed, nv);
+    ALLOC(S->d_tex, nv);
+    ALLOC(S->d_pp, np);
+    ALLOC(S->d_pair_acc, (size_t)kAcc * np);
+    ALLOC(S->d_pair_loss, np);
+    ALLOC(S->d_contrib, (size_t)12 * np);
+    ALLOC(S->d_grad, (size_t)6 * nv);
+    ALLOC(S->d_grad_tmp, (size_t)6 * nv);
+    ALLOC(S->d_loss, n_scenes);
+    ALLOC(S->d_m, (size_t)6 * nv);
+    ALLOC(S->d_v, (size_t)6 * nv);
+    ALLOC(S->d_lambda, 1);
+    ALLOC(S->d_T, (size_t)12 * nv);
+    ALLOC(S->d_T_eval, (size_t)12 * nv);
+    ALLOC(S->d_step, 1);
+    ALLOC(S->d_flag, 1);
+    ALLOC(S->d_done, 1);
+    CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
+    cudaStream_t st = S->stream;
+    if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(S->d_map, 0, (size_t)S->map_elems * map_size, st));
+    vbase = 0;
+    for (int s = 0; s < n_scenes; ++s) {
+      const epo_scene_desc& d = descs[s];
+      for (int v = 0; v < d.n_views; ++v) {
+        const ViewDev& w = S->views[vbase + v];
+        CK(cudaMemcpy2DAsync((uint8_t*)S->d_map + w.map_off * map_size, (size_t)w.pitch * map_size,
+                             d.views[v].map, (size_t)w.W * map_size, (size_t)w.W * map_size, w.H,
+                             d.pointers_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      }
+      vbase += d.n_views;
+    }
+    CK(cudaMemcpyAsync(S->d_views, S->views.data(), nv * sizeof(ViewDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_src_pair_off, S->src_pair_off.data(), (nv + 1) * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_src_pair_ids, S->src_pair_ids.data(), np * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pair_src, S->pair_src.data(), np * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pair_dst, S->pair_dst.data(), np * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pair_scene, S->pair_scene.data(), np * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_scene_pair_off, S->scene_pair_off.data(), (n_scenes + 1) * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_scene_active, S->scene_active.data(), n_scenes * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pose_pair_off, pose_off.data(), (nv + 1) * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pose_pair_ref, pose_ref.data(), 2 * np * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_active, S->active.data(), np, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_fixed, fixed.data(), nv, cudaMemcpyHostToDevice, st));
+    // identity poses, zero optimiser state
+    std::vector<double> I(12 * (size_t)nv, 0.0);
+    for (int v = 0; v < nv; ++v) I[12 * v] = I[12 * v + 5] = I[12 * v + 10] = 1.0;
+    CK(cudaMemcpyAsync(S->d_T, I.data(), I.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(S->d_m, 0, 6 * (size_t)nv * 8, st));
+    CK(cudaMemsetAsync(S->d_v, 0, 6 * (size_t)nv * 8, st));
+    CK(cudaMemsetAsync(S->d_step, 0, 8, st));
+    CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
+    CK(cudaMemsetAsync(S->d_done, 0, 4, st));
+    CK(cudaMemsetAsync(S->d_pair_acc, 0, (size_t)kAcc * np * 8, st));
+    // validate maps on the device
+    CK(launch_map_check(S->d_map, S->map_dtype, S->map_elems, S->d_flag, st));
+    CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*S->h_flag != 0)
+      return fail(nullptr, EPO_ERR_INVALID_ARG, "map with a non-finite or negative value");
+    CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
+    // texture path: one gather-capable 2-D CUDA array per view (texture gather is defined
+    // for arrays created with cudaArrayTextureGather), filled from the atlas
+    S->tex.assign(nv, 0);
+    S->arrays.assign(nv, nullptr);
+    const cudaChannelFormatDesc cfd = S->map_dtype ? cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned)
+                                                   : cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    for (int v = 0; v < nv; ++v) {
+      const ViewDev& w = S->views[v];
+      CK(cudaMallocArray(&S->arrays[v], &cfd, w.W, w.H, cudaArrayTextureGather));
+      S->device_bytes += (int64_t)w.W * w.H * (int64_t)map_size;
+      CK(cudaMemcpy2DToArrayAsync(S->arrays[v], 0, 0, (uint8_t*)S->d_map + w.map_off * map_size,
+                                  (size_t)w.pitch * map_size, (size_t)w.W * map_size, w.H,
+                                  cudaMemcpyDeviceToDevice, st));
+      cudaResourceDesc rd;
+      memset(&rd, 0, sizeof(rd));
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = S->arrays[v];
+      cudaTextureDesc td;
+      memset(&td, 0, sizeof(td));
+      td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      CK(cudaCreateTextureObject(&S->tex[v], &rd, &td, nullptr));
+    }
+    std::vector<unsigned long long> th(S->tex.begin(), S->tex.end());
+    CK(cudaMemcpyAsync(S->d_tex, th.data(), nv * 8, cudaMemcpyHostToDevice, st));
+    if (o.timing) {
+      CK(cudaEventCreate(&S->ev0));
+      CK(cudaEventCreate(&S->ev1));
+    }
+    // schedule
+    S->block = o.block_threads ? o.block_threads : 256;
+    S->rpt = o.records_per_thread ? o.records_per_thread : 4;
+    S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG;
+    epo_status bs = build_tiles(S, S->block * S->rpt);
+    if (bs != EPO_OK) return bs;
+    CK(cudaStreamSynchronize(st));
+  }
+  *out = S;
+  return EPO_OK;
+}
+
+void destroy_impl(epo_scene* S) {
+  if (!S) return;
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->ev0) cudaEventDestroy(S->ev0);
+  if (S->ev1) cudaEventDestroy(S->ev1);
+  for (auto t : S->tex)
+    if (t) cudaDestroyTextureObject(t);
+  for (auto a : S->arrays)
+    if (a) cudaFreeArray(a);
+  for (auto& b : S->bufs)
+    if (b.p) cudaFree(b.p);
+  if (S->h_flag) cudaFreeHost(S->h_flag);
+  if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
+  delete S;
+}
+
+}  // namespace
+
+extern "C" {
+
+void epo_default_options(epo_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->huber_delta = 1.0;
+  o->lambda0 = 10.0;
+  o->lambda1 = 6.0;
+  o->lambda_steps = 1000;
+  o->eps_z = 1e-6;
+  o->norm_mode = EPO_NORM_VALID;
+  o->lr_rot = 2e-3;
+  o->lr_trans = 2e-2;
+  o->beta1 = 0.9;
+  o->beta2 = 0.999;
+  o->adam_eps = 1e-12;
+  o->autotune = 0;
+  o->gather = EPO_GATHER_AUTO;
+}
+
+int32_t epo_abi_version(void) { return EPO_ABI_VERSION; }
+
+epo_status epo_create_scene(const epo_scene_desc* desc, const epo_options* opts, void* cuda_stream,
+                            epo_scene_t* out) {
+  return epo_create_batch(1, desc, opts, cuda_stream, out);
+}
+
+epo_status epo_create_batch(int32_t n_scenes, const epo_scene_desc* descs, const epo_options* opts,
+                            void* cuda_stream, epo_scene_t* out) {
+  if (out) *out = nullptr;
+  epo_scene* S = new (std::nothrow) epo_scene();
+  if (!S) return fail(nullptr, EPO_ERR_OOM, "host allocation failed");
+  epo_status st = create_impl(n_scenes, descs, opts, cuda_stream, out, S);
+  if (st != EPO_OK) {
+    if (!S->err.empty()) g_create_error = S->err;
+    destroy_impl(S);
+    if (out) *out = nullptr;
+  }
+  return st;
+}
+
+void epo_destroy_scene(epo_scene_t S) {
+  if (S) cudaStreamSynchronize(S->stream);
+  destroy_impl(S);
+}
+
+const char* epo_last_error(epo_scene_t S) { return S ? S->err.c_str() : g_create_error.c_str(); }
+
+epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
+  if (!S || !info) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  info->n_scenes = S->n_scenes;
+  info->n_views = S->n_views;
+  info->n_pairs = S->n_pairs;
+  info->n_records = S->n_records;
+  info->n_dropped = S->n_dropped;
+  int64_t ev = 0;
+  for (int p = 0; p < S->n_pairs; ++p)
+    if (S->active[p]) ev += S->views[S->pair_src[p]].n_rec;
+  info->evals_per_step = ev;
+  info->device_bytes = S->device_bytes;
+  info->record_bytes = S->n_records * (S->rec_dtype ? 8 : 16);
+  info->map_bytes = S->map_elems * (S->map_dtype ? 2 : 4);
+  info->n_tiles = S->n_tiles;
+  info->gather = S->gather;
+  info->block_threads = S->block;
+  info->records_per_thread = S->rpt;
+  info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
+  return EPO_OK;
+}
+
+epo_status epo_set_poses(epo_scene_t S, const double* T) {
+  if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  for (int64_t k = 0; k < 12 * (int64_t)S->n_views; ++k)
+    if (!isfinite(T[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
+  CK(cudaMemcpyAsync(S->d_T, T, 12 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_poses(epo_scene_t S, double* T) {
+  if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(T, S->d_T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_set_poses_dev(epo_scene_t S, const double* T) {
+  if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(S->d_T, T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_poses_dev(epo_scene_t S, double* T) {
+  if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(T, S->d_T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_state(epo_scene_t S, int64_t* step, double* m, double* v) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (step) CK(cudaMemcpyAsync(step, S->d_step, 8, cudaMemcpyDeviceToHost, S->stream));
+  if (m) CK(cudaMemcpyAsync(m, S->d_m, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (v) CK(cudaMemcpyAsync(v, S->d_v, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_set_state(epo_scene_t S, int64_t step, const double* m, const double* v) {
+  if (!S || step < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step");
+  CK(cudaMemcpyAsync(S->d_step, &step, 8, cudaMemcpyHostToDevice, S->stream));
+  if (m) CK(cudaMemcpyAsync(S->d_m, m, 6 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
+  else CK(cudaMemsetAsync(S->d_m, 0, 6 * (size_t)S->n_views * 8, S->stream));
+  if (v) CK(cudaMemcpyAsync(S->d_v, v, 6 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
+  else CK(cudaMemsetAsync(S->d_v, 0, 6 * (size_t)S->n_views * 8, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_loss_and_grad_dev(epo_scene_t S, double* loss_dev, double* grad_dev) {
+  if (!S || !loss_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  st = enqueue_loss_grad(S, S->stream, S->d_T);
+  if (st != EPO_OK) return st;
+  CK(cudaMemcpyAsync(loss_dev, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToDevice, S->stream));
+  if (grad_dev)
+    CK(cudaMemcpyAsync(grad_dev, S->d_grad, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_loss_and_grad(epo_scene_t S, double* loss, double* grad) {
+  if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  st = enqueue_loss_grad(S, S->stream, S->d_T);
+  if (st != EPO_OK) return st;
+  CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (grad) CK(cudaMemcpyAsync(grad, S->d_grad, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (*S->h_flag & 1) {
+    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient");
+  }
+  return EPO_OK;
+}
+
+epo_status epo_pair_stats(epo_scene_t S, double* stats) {
+  if (!S || !stats) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(stats, S->d_pair_acc, (size_t)kAcc * S->n_pairs * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev) {
+  if (!S || !loss_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
+  StepArgs a = step_args(S, S->d_T_eval, nullptr);
+  CK(launch_pair_setup(a, MODE_FWD, S->stream));
+  st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->stream);
+  if (st != EPO_OK) return st;
+  CK(launch_finalize(a, 0, S->stream));
+  CK(cudaMemcpyAsync(loss_dev, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToDevice, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* dloss_dev,
+                            double* grad_xi_dev) {
+  if (!S || !dloss_dev || !grad_xi_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
+  StepArgs a = step_args(S, S->d_T_eval, dloss_dev);
+  CK(launch_pair_setup(a, MODE_BWD, S->stream));
+  epo_status st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->stream);
+  if (st != EPO_OK) return st;
+  CK(launch_finalize(a, 1, S->stream));
+  CK(launch_apply_left_jacobian(xi_dev, S->d_grad, grad_xi_dev, S->n_views, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_step_async(epo_scene_t S, int32_t n_steps) {
+  if (!S || n_steps < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step count");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  st = ensure_graph(S);
+  if (st != EPO_OK) return st;
+  for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(S->graph, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_check(epo_scene_t S) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (*S->h_flag & 1) {
+    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
+  }
+  return EPO_OK;
+}
+
+epo_status epo_last_loss(epo_scene_t S, double* loss) {
+  if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_kernel_time(epo_scene_t S, float* ms) {
+  if (!S || !ms) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  if (!S->ev0 || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
+  CK(cudaEventSynchronize(S->ev1));
+  CK(cudaEventElapsedTime(ms, S->ev0, S->ev1));
+  return EPO_OK;
+}
+
+epo_status epo_step(epo_scene_t S, int32_t n_steps) {
+  epo_status st = epo_step_async(S, n_steps);
+  if (st != EPO_OK) return st;
+  return epo_check(S);
+}
+
+epo_status epo_step_plain(epo_scene_t S, int32_t n_steps) {
+  if (!S || n_steps < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step count");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  for (int k = 0; k < n_steps; ++k) {
+    st = enqueue_step(S, S->stream);
+    if (st != EPO_OK) return st;
+  }
+  return EPO_OK;
+}
+
+epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
+  if (!S || n < 0 || (n > 0 && !ids)) return fail(S, EPO_ERR_INVALID_ARG, "invalid subset");
+  std::vector<uint8_t> act(S->n_pairs, n == 0 ? 1 : 0);
+  for (int k = 0; k < n; ++k) {
+    if (ids[k] < 0 || ids[k] >= S->n_pairs) return fail(S, EPO_ERR_INVALID_ARG, "pair id out of range");
+    if (act[ids[k]]) return fail(S, EPO_ERR_INVALID_ARG, "duplicate pair id");
+    act[ids[k]] = 1;
+  }
+  S->active = act;
+  for (int s = 0; s < S->n_scenes; ++s) {
+    int c = 0;
+    for (int p = S->scene_pair_off[s]; p < S->scene_pair_off[s + 1]; ++p) c += act[p];
+    S->scene_active[s] = c;
+  }
+  CK(cudaMemcpyAsync(S->d_active, S->active.data(), S->n_pairs, cudaMemcpyHostToDevice, S->stream));
+  CK(cudaMemcpyAsync(S->d_scene_active, S->scene_active.data(), S->n_scenes * 4, cudaMemcpyHostToDevice, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_autotune(epo_scene_t S) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  S->tuned = true;  // also guards against recursion through maybe_autotune
+  const int gathers[2] = {GATHER_LDG, GATHER_TEX};
+  const int rpts[3] = {2, 4, 8};
+  const int blocks[3] = {128, 256, 512};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  StepArgs a = step_args(S, S->d_T, nullptr);
+  float best = 1e30f;
+  int bg = S->gather, br = S->rpt, bb = S->block;
+  for (int g : gathers)
+    for (int r : rpts)
+      for (int b : blocks) {
+        if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
+        if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
+        float tot = 0.f;
+        for (int it = 0; it < 4; ++it) {
+          CK(launch_pair_setup(a, MODE_FUSED, S->stream));
+          CK(cudaEventRecord(e0, S->stream));
+          epo_status st = run_edge(S, MODE_FUSED, g, r, b, S->stream);
+          if (st != EPO_OK) return st;
+          CK(cudaEventRecord(e1, S->stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (it > 0) tot += ms;  // first launch is a warm-up
+        }
+        if (tot < best) {
+          best = tot;
+          bg = g; br = r; bb = b;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S->gather = bg;
+  S->rpt = br;
+  S->block = bb;
+  S->graph_dirty = true;
+  return build_tiles(S, bb * br);
+}
+
+epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, float* map_dev,
+                              void* cuda_stream) {
+  epo_scene* S = nullptr;
+  if (!edges_dev || !map_dev || W < 1 || H < 1)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid distance-field arguments");
+  if (H > edt_max_height()) return fail(nullptr, EPO_ERR_INVALID_ARG, "distance field: H above the supported maximum");
+  CK(launch_edt(edges_dev, W, H, map_dev, (cudaStream_t)cuda_stream));
+  return EPO_OK;
+}
+
+epo_status epo_round_bf16(const float* src, uint16_t* dst, int64_t n, void* cuda_stream) {
+  epo_scene* S = nullptr;
+  if (!src || !dst || n < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid bf16 rounding arguments");
+  if (n == 0) return EPO_OK;
+  CK(launch_round_bf16(src, dst, n, (cudaStream_t)cuda_stream));
+  return EPO_OK;
+}
+
+}  // extern "C"

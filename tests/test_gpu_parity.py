@@ -1,0 +1,443 @@
+"""GPU kernels vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (FP32 path, stated by the arithmetic):
+  * loss: relative 1e-5;  gradient: max_i ||g_i - g_i^oracle|| <= 1e-4 max_i ||g_i^oracle||.
+    FP32 rounding of T_ji and of the projection moves a sample by ~1e-7 of its pixel
+    coordinate (<= 5e-5 px at 518 px); with |grad DTF| <= 1 the per-sample distance moves by
+    the same amount, which averages to ~1e-6 relative over thousands of samples.
+  * n_valid per pair is an integer decided by FP comparisons of the projected position
+    against the image border (and the depth against eps_z).  The kernel decides in FP32, the
+    oracle in FP64; they may differ only on samples the oracle finds within 1e-3 px of a
+    border (its pair_near count), so |n_gpu - n_oracle| <= near is required exactly.
+  * BF16 maps / FP16 depth: against the oracle fed the same rounded values ("kernel parity")
+    the FP32 tolerances hold; against the oracle fed the full-precision inputs ("precision
+    cost") loss and gradient agree to 1e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import (bf16_bits, bf16_to_f32, grad_rel_err, gpu_scene, oracle_maps_f32, rot_err_deg,
+                           scene_part, trans_err)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA GPU required", allow_module_level=True)
+
+import paper_2607_00579_gb300 as epo  # noqa: E402
+
+LOSS_RTOL = 1e-5
+GRAD_RTOL = 1e-4
+PAIR_RHO_RTOL = 1e-5
+PAIR_GRAD_RTOL = 1e-4
+CELL_FLIPS = 4  # adjacent-cell choices per pair allowed between FP32 and FP64 (see module doc)
+
+
+@pytest.fixture(scope="module")
+def ring8():
+    sc = synth.make_scene(synth.RING8_128x96)
+    maps = oracle_maps_f32(sc)
+    return sc, maps
+
+
+def oracle_of(sc, maps, rec=None):
+    return oracle.scene_from_synth(sc, [m.astype(np.float64) for m in maps],
+                                   rec=None if rec is None else rec)
+
+
+def huber_max(lam, delta):
+    return delta * (lam - 0.5 * delta) if lam > delta else 0.5 * lam * lam
+
+
+def pose4(T12):
+    M = np.eye(4)
+    M[:3] = np.asarray(T12).reshape(3, 4)
+    return M
+
+
+def allowances(o, pairs, T, n_views, lam, delta):
+    """What FP32-vs-FP64 decisions may legitimately change.
+
+    A validity flip (a sample within 1e-3 px of the border, counted by the oracle) moves one
+    sample in or out of a pair's mean: the pair loss moves by at most (H(lambda) + l_p)/n and
+    the pair's gradient by at most one sample's term plus a 1/n rescale.  Independently, a
+    sample within ~1e-4 px of a bilinear cell line may take the neighbouring cell, changing
+    its slope term by at most twice its size; CELL_FLIPS such samples are allowed per pair.
+    The target pose receives a pair's 6-vector as is, the source pose through -Ad(T_ji)^T,
+    whose norm is at most 2 + |t_ji|."""
+    near = o["pair_near"].astype(float)
+    n = o["pair_stats"][:, 1]
+    P = len(near)
+    w = near / np.maximum(n - near, 1.0)
+    allow_L = 2.0 / P * float(np.sum(w * (huber_max(lam, delta) + o["pair_loss"])))
+    per_pair = 2.0 / P * (2.0 * near + 2.0 * CELL_FLIPS) * o["pair_maxterm"] / np.maximum(n - near, 1.0)
+    allow_g = np.zeros(n_views)
+    for p, (i, j) in enumerate(np.asarray(pairs)):
+        if per_pair[p] == 0:
+            continue
+        tji = (pose4(T[j]) @ np.linalg.inv(pose4(T[i])))[:3, 3]
+        allow_g[j] += per_pair[p]
+        allow_g[i] += per_pair[p] * (2.0 + np.linalg.norm(tji))
+    return allow_L, allow_g
+
+
+def check_against_oracle(loss_g, grad_g, o, pairs, T, lam=10.0, delta=1.0, stats=None, grad_scale=1.0,
+                         slope_pairs=None):
+    """slope_pairs: boolean mask of the pairs whose per-pair slope sums are compared (default all)."""
+    allow_L, allow_g = allowances(o, pairs, T, len(grad_g), lam, delta)
+    assert abs(loss_g - o["loss"]) <= LOSS_RTOL * abs(o["loss"]) + allow_L, (loss_g, o["loss"], allow_L)
+    err = np.linalg.norm(np.asarray(grad_g) - o["grad"], axis=1)
+    gmax = np.linalg.norm(o["grad"], axis=1).max()
+    bad = err > GRAD_RTOL * gmax + grad_scale * allow_g
+    assert not bad.any(), (err[bad], gmax, allow_g[bad])
+    if stats is not None:
+        near = o["pair_near"]
+        dn = np.abs(stats[:, 1] - o["pair_stats"][:, 1])
+        assert np.all(dn <= near), (dn.max(), near[dn.argmax()])
+        same = dn == 0
+        d_rho = np.abs(stats[same, 0] - o["pair_stats"][same, 0])
+        assert np.all(d_rho <= PAIR_RHO_RTOL * np.abs(o["pair_stats"][same, 0]) + 1e-6)
+        if slope_pairs is not None:
+            same = same & slope_pairs
+        d_g = np.abs(stats[same, 2:] - o["pair_stats"][same, 2:])
+        tol = PAIR_GRAD_RTOL * o["pair_abs"][same] + 2.0 * CELL_FLIPS * o["pair_maxterm"][same, None]
+        assert np.all(d_g <= tol), (d_g / np.maximum(o["pair_abs"][same], 1e-300)).max()
+
+
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("gather", [epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX])
+@pytest.mark.parametrize("rpt,block", [(4, 256), (2, 128), (8, 512)])
+def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, gather=gather, records_per_thread=rpt, block_threads=block)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    st = s.pair_stats()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=st)
+
+
+def test_gather_paths_and_schedules_agree(ring8):
+    sc, maps = ring8
+    res = []
+    for gather, rpt, block in [(1, 4, 256), (2, 4, 256), (1, 8, 128), (2, 2, 512)]:
+        s = gpu_scene(sc, maps, gather=gather, records_per_thread=rpt, block_threads=block)
+        s.set_poses(sc.T_init)
+        res.append(s.loss_and_grad())
+    for l, g in res[1:]:
+        assert l[0] == pytest.approx(res[0][0][0], rel=1e-6)
+        assert grad_rel_err(g, res[0][1]) < 1e-6
+
+
+def test_norm_all_mode(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, norm_mode=epo.EPO_NORM_ALL)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0, norm_mode=oracle.NORM_ALL)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init)
+
+
+def test_lambda_and_huber_options(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, lambda0=2.5, lambda1=2.5, huber_delta=0.5)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=2.5, delta=0.5)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, lam=2.5, delta=0.5, stats=s.pair_stats())
+
+
+def tiny_edge_scene():
+    """Hand-made records: on the image border, on cell lines, behind the camera, ragged tile
+    tails (counts not multiples of any tile), an empty source view and a self pair."""
+    rng = np.random.default_rng(7)
+    n, W, H = 4, 33, 17
+    f = 20.0
+    K = np.tile([f, f, (W - 1) / 2, (H - 1) / 2], (n, 1))
+    T = np.zeros((n, 12))
+    from scipy.spatial.transform import Rotation
+    for v in range(n):
+        R = Rotation.from_rotvec(rng.normal(0, 0.03, 3)).as_matrix()
+        T[v] = np.concatenate([R, rng.normal(0, 0.05, 3)[:, None]], 1).reshape(-1)
+    counts = [1037, 0, 3, 517]
+    recs, off = [], [0]
+    for v in range(n):
+        c = counts[v]
+        u = rng.integers(0, W, c).astype(np.float32)
+        vv = rng.integers(0, H, c).astype(np.float32)
+        z = rng.uniform(3.0, 5.0, c).astype(np.float32)
+        if c > 10:
+            u[:4] = [0, W - 1, 0, W - 1]
+            vv[:4] = [0, 0, H - 1, H - 1]
+            z[4] = -1.0  # dropped at creation
+        r = np.zeros((c, 4), np.float32)
+        r[:, 0], r[:, 1], r[:, 2] = u, vv, z
+        recs.append(r)
+        off.append(off[-1] + c)
+    rec = np.concatenate(recs)
+    maps = [rng.uniform(0, 5, (H, W)).astype(np.float32) for _ in range(n)]
+    pairs = np.array([(0, 1), (1, 0), (0, 0), (2, 3), (3, 2), (0, 3), (3, 0), (2, 0)], np.int32)
+    return dict(W=[W] * n, H=[H] * n, K=K, rec_off=np.array(off), rec=rec, maps=maps, pairs=pairs,
+                fixed=None), T
+
+
+def test_edge_cases_ragged_empty_border_self_pair():
+    part, T = tiny_edge_scene()
+    s = epo.Scene([part])
+    assert s.info().n_dropped == 2
+    s.set_poses(T)
+    loss, grad = s.loss_and_grad()
+    keep = part["rec"][:, 2] > 0
+    rec = part["rec"][keep]
+    cnt = [int(np.sum(keep[part["rec_off"][v]:part["rec_off"][v + 1]])) for v in range(4)]
+    off = np.concatenate([[0], np.cumsum(cnt)])
+    os_ = oracle.OracleScene(part["W"], part["H"], part["K"], off, rec,
+                             [m.astype(np.float64) for m in part["maps"]], part["pairs"])
+    o = os_.loss_grad(T, lam=10.0)
+    st = s.pair_stats()
+    # the self pair (0, 0) projects every record exactly onto its own integer pixel, where
+    # the bilinear slope is one-sided and FP32 / FP64 rounding picks the cell; its slope sums
+    # are not comparable (its target and source contributions cancel in the pose gradient)
+    self_pair = part["pairs"][:, 0] == part["pairs"][:, 1]
+    check_against_oracle(loss[0], grad, o, part["pairs"], T, stats=st, slope_pairs=~self_pair)
+    assert st[1, 1] == 0 and st[1, 0] == 0  # empty source view
+
+
+def test_all_samples_invalid_gives_zero_pair_loss():
+    part, T = tiny_edge_scene()
+    T2 = T.copy()
+    from scipy.spatial.transform import Rotation
+    # view 3 turned around: nothing from view 0 or 2 lands in front of it
+    M = T2[3].reshape(3, 4)
+    T2[3] = np.concatenate([Rotation.from_rotvec([0, math.pi, 0]).as_matrix() @ M[:, :3], M[:, 3:]], 1).reshape(-1)
+    s = epo.Scene([part])
+    s.set_poses(T2)
+    loss, grad = s.loss_and_grad()
+    st = s.pair_stats()
+    assert st[3, 1] == 0 and st[5, 1] == 0
+    assert np.isfinite(loss).all() and np.isfinite(grad).all()
+
+
+# ---------------------------------------------------------------------------------------------
+def test_distance_field_kernel_is_exact(ring8):
+    sc, _ = ring8
+    rng = np.random.default_rng(3)
+    cases = [e for e in sc.edges[:3]]
+    cases += [(rng.random((H, W)) < d).astype(np.uint8) for (H, W, d) in
+              [(17, 33, 0.05), (1, 9, 0.3), (40, 1, 0.1), (64, 70, 0.0), (50, 200, 0.001), (392, 518, 0.02)]]
+    for e in cases:
+        g = epo.distance_field(torch.from_numpy(e).cuda()).cpu().numpy()
+        ref = oracle.edt(e).astype(np.float32)
+        assert np.array_equal(g, ref)
+
+
+def test_bf16_rounding_kernel_matches_rne():
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(0, 600, 100000), np.arange(0, 1000, 0.25)]).astype(np.float32)
+    g = epo.round_bf16(torch.from_numpy(x).cuda()).cpu().numpy().view(np.uint16)
+    assert np.array_equal(g, bf16_bits(x))
+
+
+# ---------------------------------------------------------------------------------------------
+def test_fp16_depth_bf16_map_kernel_parity_and_precision_cost(ring8):
+    sc, maps = ring8
+    bits = [bf16_bits(m) for m in maps]
+    rec16 = synth.records_f16(sc.rec)
+    s = gpu_scene(sc, bits, rec=rec16, record_dtype=epo.EPO_F16, map_dtype=epo.EPO_BF16)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    # kernel parity: the oracle sees exactly the stored values
+    o_same = oracle.scene_from_synth(sc, [bf16_to_f32(b).astype(np.float64) for b in bits],
+                                     rec=synth.records_f16_widened(sc.rec)).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o_same, sc.pairs, sc.T_init, stats=s.pair_stats())
+    # precision cost: the oracle sees the full-precision inputs
+    o_full = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    assert abs(loss[0] - o_full["loss"]) <= 1e-2 * o_full["loss"]
+    assert grad_rel_err(grad, o_full["grad"]) <= 1e-2
+
+
+# ---------------------------------------------------------------------------------------------
+def test_optimisation_matches_oracle_and_improves(ring8):
+    sc, maps = ring8
+    kw = dict(lr_rot=2e-3, lr_trans=5e-2)
+    s = gpu_scene(sc, maps, **kw)
+    s.set_poses(sc.T_init)
+    s.step(50)
+    Tg = s.get_poses()
+    To, _, _, hist = oracle_of(sc, maps).optimize(sc.T_init, sc.fixed, 50, **kw)
+    assert rot_err_deg(Tg, To).max() <= 0.01
+    assert trans_err(Tg, To, sc.scale).max() <= 1e-4
+    assert rot_err_deg(Tg, sc.T_gt).mean() < rot_err_deg(sc.T_init, sc.T_gt).mean()
+    assert trans_err(Tg, sc.T_gt, sc.scale).mean() < trans_err(sc.T_init, sc.T_gt, sc.scale).mean()
+    assert np.array_equal(Tg[0], sc.T_init[0])
+    step, m, v = s.get_state()
+    assert step == 50
+
+
+def test_graph_step_equals_plain_step(ring8):
+    sc, maps = ring8
+    a = gpu_scene(sc, maps)
+    b = gpu_scene(sc, maps)
+    a.set_poses(sc.T_init)
+    b.set_poses(sc.T_init)
+    a.step(10)
+    b.step_plain(10)
+    b.check()
+    # identical kernels; only the order of FP64 atomics differs between runs
+    assert np.abs(a.get_poses() - b.get_poses()).max() < 1e-9
+
+
+def test_checkpoint_resume_equals_uninterrupted(ring8):
+    sc, maps = ring8
+    a = gpu_scene(sc, maps)
+    a.set_poses(sc.T_init)
+    a.step(20)
+    b = gpu_scene(sc, maps)
+    b.set_poses(sc.T_init)
+    b.step(10)
+    T, st = b.get_poses(), b.get_state()
+    c = gpu_scene(sc, maps)
+    c.set_poses(T)
+    c.set_state(*st)
+    c.step(10)
+    assert np.abs(a.get_poses() - c.get_poses()).max() < 1e-9
+
+
+def test_nonfinite_pose_refuses_update(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    T = torch.tensor(sc.T_init, dtype=torch.float64, device="cuda")
+    T[2, 3] = float("nan")
+    epo._binding.epo_set_poses_dev(s.handle, T)
+    with pytest.raises(epo.EpoError) as e:
+        s.step(3)
+    assert e.value.status == epo._binding.EPO_ERR_NUMERIC
+    after = s.get_poses()
+    assert np.array_equal(after[1], sc.T_init[1])
+    assert s.get_state()[0] == 0
+
+
+def test_nan_map_is_rejected(ring8):
+    sc, maps = ring8
+    bad = [m.copy() for m in maps]
+    bad[3][5, 5] = np.nan
+    with pytest.raises(epo.EpoError) as e:
+        gpu_scene(sc, bad)
+    assert e.value.status == epo._binding.EPO_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------------------------------------
+def test_autograd_forward_backward(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    ref_loss, ref_grad = s.loss_and_grad()
+    xi = torch.zeros((sc.n_views, 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    L = epo.EdgeLoss.apply(xi, s)
+    L.sum().backward()
+    assert L.item() == pytest.approx(ref_loss[0], rel=1e-12)
+    assert grad_rel_err(xi.grad.cpu().numpy(), ref_grad) < 1e-9
+    # at a non-zero twist: d/dxi L(Exp(xi) T) = J_l(xi)^T g_left(Exp(xi) T)
+    rng = np.random.default_rng(5)
+    x = rng.normal(0, 0.01, (sc.n_views, 6))
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    L = epo.EdgeLoss.apply(xt, s)
+    (3.0 * L.sum()).backward()
+    Tx = np.stack([(np.vstack([oracle.se3_exp(x[v]).reshape(3, 4), [0, 0, 0, 1]])
+                    @ np.vstack([sc.T_init[v].reshape(3, 4), [0, 0, 0, 1]]))[:3].reshape(-1)
+                   for v in range(sc.n_views)])
+    o = oracle_of(sc, maps).loss_grad(Tx, lam=10.0)
+    assert L.item() == pytest.approx(o["loss"], rel=LOSS_RTOL)
+    want = 3.0 * np.stack([oracle.se3_left_jacobian(x[v]).T @ o["grad"][v] for v in range(sc.n_views)])
+    assert grad_rel_err(xt.grad.cpu().numpy(), want) <= GRAD_RTOL
+
+
+def test_batched_scenes_equal_individual_scenes():
+    specs = synth.batch64_uneven_specs(n_scenes=3)
+    for sp in specs:
+        sp.width, sp.height, sp.n_views = 160, 120, min(sp.n_views, 12)
+    scenes = [synth.make_scene(sp) for sp in specs]
+    maps = [oracle_maps_f32(sc) for sc in scenes]
+    b = epo.Scene([scene_part(sc, m) for sc, m in zip(scenes, maps)])
+    b.set_poses(np.concatenate([sc.T_init for sc in scenes]))
+    lb, gb = b.loss_and_grad()
+    off = 0
+    for k, (sc, m) in enumerate(zip(scenes, maps)):
+        s = gpu_scene(sc, m)
+        s.set_poses(sc.T_init)
+        l1, g1 = s.loss_and_grad()
+        assert lb[k] == pytest.approx(l1[0], rel=1e-12)
+        assert grad_rel_err(gb[off:off + sc.n_views], g1) < 1e-10
+        o = oracle_of(sc, m).loss_grad(sc.T_init, lam=10.0)
+        check_against_oracle(lb[k], gb[off:off + sc.n_views], o, sc.pairs, sc.T_init)
+        off += sc.n_views
+
+
+def test_pair_subset(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    ids = np.array([3, 17, 40, 41, 55])
+    s.set_pair_subset(ids)
+    loss, grad = s.loss_and_grad()
+    o = oracle.OracleScene(sc.W, sc.H, sc.K, sc.rec_off, sc.rec,
+                           [m.astype(np.float64) for m in maps], sc.pairs[ids]).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs[ids], sc.T_init)
+    assert s.info().evals_per_step == int(np.diff(sc.rec_off)[sc.pairs[ids, 0]].sum())
+    s.set_pair_subset([])
+    l2, _ = s.loss_and_grad()
+    assert l2[0] == pytest.approx(oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)["loss"], rel=LOSS_RTOL)
+
+
+def test_autotune_keeps_results(ring8):
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, autotune=1)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=s.pair_stats())
+    i = s.info()
+    assert i.records_per_thread in (2, 4, 8) and i.block_threads in (128, 256, 512)
+
+
+# ---------------------------------------------------------------------------------------------
+# full size: the 32-view 518x392 ring in the benchmark's launch configuration
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def ring32():
+    sc = synth.make_scene(synth.RING32_518x392)
+    e = [torch.from_numpy(x).cuda() for x in sc.edges]
+    maps = [epo.distance_field(x).cpu().numpy() for x in e]
+    return sc, maps
+
+
+def test_full_size_sampled_pairs_match_oracle(ring32):
+    sc, maps = ring32
+    for v in (0, 7, 31):
+        assert np.array_equal(maps[v], oracle.edt(sc.edges[v]).astype(np.float32))
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    st = s.pair_stats()
+    rng = np.random.default_rng(11)
+    ids = np.sort(rng.choice(sc.n_pairs, 24, replace=False))
+    o = oracle.OracleScene(sc.W, sc.H, sc.K, sc.rec_off, sc.rec, [m.astype(np.float64) for m in maps],
+                           sc.pairs[ids]).loss_grad(sc.T_init, lam=10.0)
+    # per-pair sums of the sampled pairs, computed by the oracle one pair at a time
+    check_against_oracle(float(o["loss"]), o["grad"], o, sc.pairs[ids], sc.T_init)  # self-consistency
+    sub = st[ids]
+    dn = np.abs(sub[:, 1] - o["pair_stats"][:, 1])
+    assert np.all(dn <= o["pair_near"])
+    same = dn == 0
+    assert np.all(np.abs(sub[same, 0] - o["pair_stats"][same, 0]) <= PAIR_RHO_RTOL * o["pair_stats"][same, 0] + 1e-6)
+    tol = PAIR_GRAD_RTOL * o["pair_abs"][same] + 2.0 * CELL_FLIPS * o["pair_maxterm"][same, None]
+    assert np.all(np.abs(sub[same, 2:] - o["pair_stats"][same, 2:]) <= tol)
+    # the whole loss and gradient (the oracle runs all 256 pairs once)
+    full = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, full, sc.pairs, sc.T_init, stats=st)
