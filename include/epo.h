@@ -82,7 +82,8 @@ typedef struct {
   int32_t n_views;           /* >= 1 */
   const epo_view_desc* views;
   int32_t n_pairs;           /* >= 1 */
-  const int32_t* pairs;      /* 2*n_pairs ints: (i, j) per directed pair, i != j allowed */
+  const int32_t* pairs;      /* 2*n_pairs ints: (i, j) per directed pair, i == j allowed;
+                                at most 512 pairs share one source view */
   const uint8_t* fixed;      /* n_views bytes, 1 = pose frozen by epo_step; NULL = none */
   int32_t record_dtype;      /* EPO_F32 | EPO_F16 */
   int32_t map_dtype;         /* EPO_F32 | EPO_BF16 */
@@ -100,8 +101,8 @@ typedef struct {
   double beta1, beta2, adam_eps; /* Adam moments (Section 3: 0.9, 0.999) */
   int32_t autotune;          /* 1: pick the kernel schedule by timing on first use */
   int32_t gather;            /* EPO_GATHER_* (AUTO = LDG unless autotuned) */
-  int32_t block_threads;     /* 0 = default (256); else 64..1024, multiple of 32 */
-  int32_t records_per_thread;/* 0 = default (4); 2, 4 or 8 */
+  int32_t block_threads;     /* 0 = default (256); else 64..512, multiple of 32 */
+  int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 */
   int32_t grid_blocks;       /* 0 = default (persistent: SMs x resident blocks) */
   int32_t timing;            /* 1: bracket the edge kernel with CUDA events (epo_kernel_time) */
 } epo_options;
@@ -204,9 +205,23 @@ epo_status epo_check(epo_scene_t scene);
  * evaluation or step (a step evaluates before it updates).  Synchronises. */
 epo_status epo_last_loss(epo_scene_t scene, double* loss);
 
-/* Device time in milliseconds of the edge kernel (steps a2-a7) in the most
- * recent evaluation or step; needs options.timing = 1.  Synchronises. */
+/* Samples of the most recent evaluation whose FP32 position lay within its
+ * rounding-error bound of a discontinuity (bilinear cell line, image border,
+ * depth threshold, clamp) and were re-evaluated with FP64 decisions
+ * (queued), and those that found their block's buffer full and kept their
+ * FP32 decisions (overflow, normally 0).  Synchronises. */
+epo_status epo_fixup_stats(epo_scene_t scene, int64_t* queued, int64_t* overflow);
+
+/* Device time in milliseconds of the edge kernel (lift, projection, sampling,
+ * robust penalty, adjoint and per-pair reduction) in the most recent
+ * evaluation or step; needs options.timing = 1.  Synchronises. */
 epo_status epo_kernel_time(epo_scene_t scene, float* ms);
+
+/* Device times in milliseconds of the three stages of the most recent
+ * evaluation or step: pair setup, edge kernel (with its exact re-evaluation of
+ * ambiguous samples), pose kernel (loss, gradient gather, update).  ms: 3
+ * floats.  Needs options.timing = 1.  Synchronises. */
+epo_status epo_stage_times(epo_scene_t scene, float* ms);
 
 /* Evaluate only a subset of the pairs from now on (the stochastic viewgraph
  * sub-sampling of Algorithm 3 / Appendix A.3; the draw is the caller's).

@@ -169,9 +169,13 @@ class OracleScene:
                          self.map.ctypes.data, self.n_pairs, self.pairs.ctypes.data)
 
     def loss_grad(self, T: np.ndarray, lam: float, delta: float = 1.0, eps_z: float = 1e-6,
-                  norm_mode: int = NORM_VALID, near_margin: float = 1e-3):
+                  norm_mode: int = NORM_VALID, near_margin: float = 1e-9):
         """Returns dict(loss, grad (n,6), pair_stats (P,8), pair_near (P,), pair_loss (P,),
-        pair_abs (P,6), pair_maxterm (P,))."""
+        pair_abs (P,6), pair_maxterm (P,)).
+
+        pair_near counts the samples whose position lies within near_margin pixels of the
+        image border (or whose depth lies that close to eps_z): there the validity decision
+        depends on the rounding of the arithmetic, not only on the mathematics."""
         T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12)
         prm = _Params(lam, delta, eps_z, norm_mode, near_margin)
         loss = np.zeros(1)

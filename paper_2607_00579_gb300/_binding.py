@@ -33,7 +33,7 @@ EXPORTED = [
     "epo_set_poses_dev", "epo_get_poses_dev", "epo_get_state", "epo_set_state", "epo_loss_and_grad",
     "epo_loss_and_grad_dev", "epo_pair_stats", "epo_forward_dev", "epo_backward_dev", "epo_step",
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
-    "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time",
+    "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
 ]
 
 
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "epo_round_bf16": (I32, [P, P, I64, P]),
         "epo_last_loss": (I32, [S, P]),
         "epo_kernel_time": (I32, [S, ctypes.POINTER(ctypes.c_float)]),
+        "epo_fixup_stats": (I32, [S, P, P]),
+        "epo_stage_times": (I32, [S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +217,19 @@ def epo_step_plain(scene, n): _call("epo_step_plain", scene, ctypes.c_int32(n))
 def epo_check(scene): _call("epo_check", scene)
 def epo_autotune(scene): _call("epo_autotune", scene)
 def epo_last_loss(scene, loss): _call("epo_last_loss", scene, _ptr(loss))
+
+
+def epo_fixup_stats(scene):
+    q = ctypes.c_int64(0)
+    o = ctypes.c_int64(0)
+    _call("epo_fixup_stats", scene, ctypes.byref(q), ctypes.byref(o))
+    return int(q.value), int(o.value)
+
+
+def epo_stage_times(scene):
+    ms = (ctypes.c_float * 3)()
+    _call("epo_stage_times", scene, ms)
+    return [float(x) for x in ms]
 
 
 def epo_kernel_time(scene) -> float:

@@ -84,16 +84,20 @@ struct epo_scene {
   std::vector<cudaTextureObject_t> tex;
   std::vector<cudaArray_t> arrays;
   PairParam* d_pp = nullptr;
-  double *d_pair_acc = nullptr, *d_pair_loss = nullptr, *d_contrib = nullptr, *d_grad = nullptr,
-         *d_loss = nullptr, *d_m = nullptr, *d_v = nullptr, *d_lambda = nullptr, *d_T = nullptr,
-         *d_T_eval = nullptr, *d_grad_tmp = nullptr;
+  double *d_pp64 = nullptr, *d_K64 = nullptr, *d_pair_acc = nullptr, *d_grad = nullptr,
+         *d_loss = nullptr, *d_m = nullptr, *d_v = nullptr, *d_bpow = nullptr, *d_lambda = nullptr,
+         *d_T = nullptr, *d_T_eval = nullptr;
+  unsigned int *d_qcount = nullptr, *d_qoverflow = nullptr;
+  int* d_tile_counter = nullptr;
+  int max_pairs = 1;
   int64_t* d_step = nullptr;
   int32_t* d_flag = nullptr;
   unsigned int* d_done = nullptr;
   int32_t* h_flag = nullptr;  // pinned
   int64_t device_bytes = 0;
-  // edge-kernel timing events (options.timing)
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // stage timing events (options.timing): before setup, after setup, after the edge
+  // kernel, after the pose kernel
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
   // graph of one optimisation step
   cudaGraphExec_t graph = nullptr;
@@ -147,6 +151,7 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.n_views = S->n_views;
   a.n_pairs = S->n_pairs;
   a.n_scenes = S->n_scenes;
+  a.tex = S->d_tex;
   a.pair_src = S->d_pair_src;
   a.pair_dst = S->d_pair_dst;
   a.pair_scene = S->d_pair_scene;
@@ -160,10 +165,12 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.T = T_eval;
   a.T_store = S->d_T;
   a.pp = S->d_pp;
+  a.pp64 = S->d_pp64;
   a.pair_acc = S->d_pair_acc;
-  a.pair_loss = S->d_pair_loss;
-  a.contrib = S->d_contrib;
   a.grad = S->d_grad;
+  a.bpow = S->d_bpow;
+  a.q_count = S->d_qcount;
+  a.tile_counter = S->d_tile_counter;
   a.loss = S->d_loss;
   a.m = S->d_m;
   a.v = S->d_v;
@@ -175,6 +182,7 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.lambda0 = S->opt.lambda0;
   a.lambda1 = S->opt.lambda1;
   a.lambda_steps = S->opt.lambda_steps;
+  a.inv_lambda_steps = S->opt.lambda_steps > 0 ? 1.0 / S->opt.lambda_steps : 0.0;
   a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
   a.lr_rot = S->opt.lr_rot;
   a.lr_trans = S->opt.lr_trans;
@@ -221,12 +229,19 @@ EdgeArgs edge_args(epo_scene* S) {
   a.rec = S->d_rec;
   a.map = S->d_map;
   a.views = S->d_views;
+  a.K64 = S->d_K64;
   a.tiles = S->d_tiles;
   a.n_tiles = S->n_tiles;
   a.src_pair_off = S->d_src_pair_off;
   a.src_pair_ids = S->d_src_pair_ids;
+  a.pair_src = S->d_pair_src;
   a.pair_dst = S->d_pair_dst;
   a.pp = S->d_pp;
+  a.pp64 = S->d_pp64;
+  a.q_count = S->d_qcount;
+  a.q_overflow = S->d_qoverflow;
+  a.tile_counter = S->d_tile_counter;
+  a.max_pairs = S->max_pairs;
   a.pair_active = S->d_active;
   a.tex = S->d_tex;
   a.pair_acc = S->d_pair_acc;
@@ -238,47 +253,75 @@ EdgeArgs edge_args(epo_scene* S) {
 
 int grid_for(epo_scene* S, int gather, int rpt, int block) {
   if (S->opt.grid_blocks > 0) return S->opt.grid_blocks;
-  // resident blocks per SM from the register/shared budget (<= 2048 threads per SM)
-  int per_sm = std::max(1, 2048 / block);
-  if (rpt >= 8) per_sm = std::max(1, per_sm / 2);
-  (void)gather;
-  int g = S->sm_count * per_sm;
+  // persistent grid: every SM holds as many blocks as its registers and threads allow
+  int per_sm = 0;
+  const void* k = edge_kernel_ptr(MODE_FUSED, S->rec_dtype, S->map_dtype, gather, rpt);
+  const size_t smem = edge_smem_bytes(rpt, block, S->max_pairs);
+  if (smem > 48 * 1024 && k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess || per_sm < 1)
+    per_sm = std::max(1, 1024 / block);
+  const int g = S->sm_count * per_sm;
   return std::max(1, std::min(g, std::max(S->n_tiles, 1)));
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;
+
+bool schedule_fits(epo_scene* S, int rpt, int block) {
+  return edge_smem_bytes(rpt, block, S->max_pairs) <= kMaxSmem;
+}
+
+// Record stage event k on stream s (inside a capture it becomes an event-record node).
+epo_status mark(epo_scene* S, int k, cudaStream_t s) {
+  if (!S->ev[k]) return EPO_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cap));
+  const unsigned int f = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  CK(cudaEventRecordWithFlags(S->ev[k], s, f));
+  if (k == 3) S->ev_recorded = true;
+  return EPO_OK;
+}
+
+#define MARK(k, s)                         \
+  do {                                     \
+    epo_status m_ = mark(S, (k), (s));     \
+    if (m_ != EPO_OK) return m_;           \
+  } while (0)
+
 epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, cudaStream_t s) {
+  if (!schedule_fits(S, rpt, block))
+    return fail(S, EPO_ERR_INVALID_ARG, "schedule needs more shared memory than a block has");
   epo_status st = build_tiles(S, block * rpt);
   if (st != EPO_OK) return st;
   EdgeArgs ea = edge_args(S);
   int grid = grid_for(S, gather, rpt, block);
-  // inside a stream capture the timing events become event-record nodes of the graph
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (S->ev0) CK(cudaStreamIsCapturing(s, &cap));
-  const unsigned int evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-  if (S->ev0) CK(cudaEventRecordWithFlags(S->ev0, s, evf));
   CK(launch_edge(ea, mode, S->rec_dtype, S->map_dtype, gather, rpt, block, grid, s));
-  if (S->ev1) {
-    CK(cudaEventRecordWithFlags(S->ev1, s, evf));
-    S->ev_recorded = true;
-  }
+  MARK(2, s);
   return EPO_OK;
 }
 
 // One evaluation with gradient (a1 .. a8) on stream s.
 epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval) {
   StepArgs a = step_args(S, T_eval, nullptr);
+  MARK(0, s);
   CK(launch_pair_setup(a, MODE_FUSED, s));
+  MARK(1, s);
   epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, s);
   if (st != EPO_OK) return st;
-  CK(launch_finalize(a, 1, s));
+  CK(launch_poses(a, 1, s));
+  MARK(3, s);
   return EPO_OK;
 }
 
+// One optimisation step (a1 .. a9): four kernels, no host synchronisation.
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
-  epo_status st = enqueue_loss_grad(S, s, S->d_T);
-  if (st != EPO_OK) return st;
   StepArgs a = step_args(S, S->d_T, nullptr);
-  CK(launch_retract(a, s));
+  MARK(0, s);
+  CK(launch_pair_setup(a, MODE_FUSED, s));
+  MARK(1, s);
+  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, s);
+  if (st != EPO_OK) return st;
+  CK(launch_poses(a, 2, s));
+  MARK(3, s);
   return EPO_OK;
 }
 
@@ -324,9 +367,9 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid options");
   if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
     return fail(nullptr, EPO_ERR_INVALID_ARG, "block_threads must be 64..512, a multiple of 32");
-  if (o.records_per_thread != 0 && o.records_per_thread != 2 && o.records_per_thread != 4 &&
-      o.records_per_thread != 8)
-    return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 2, 4 or 8");
+  if (o.records_per_thread != 0 && o.records_per_thread != 1 && o.records_per_thread != 2 &&
+      o.records_per_thread != 4)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 1, 2 or 4");
   if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
   S->stream = (cudaStream_t)cuda_stream;
@@ -446,7 +489,11 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   // pairs grouped by source view
   S->src_pair_off.assign(nv + 1, 0);
   for (int p = 0; p < np; ++p) S->src_pair_off[S->pair_src[p] + 1]++;
-  for (int v = 0; v < nv; ++v) S->src_pair_off[v + 1] += S->src_pair_off[v];
+  for (int v = 0; v < nv; ++v) {
+    S->max_pairs = std::max(S->max_pairs, S->src_pair_off[v + 1]);
+    S->src_pair_off[v + 1] += S->src_pair_off[v];
+  }
+  if (S->max_pairs > 512) return fail(nullptr, EPO_ERR_INVALID_ARG, "a view with more than 512 outgoing pairs");
   S->src_pair_ids.assign(np, 0);
   {
     std::vector<int32_t> fill(S->src_pair_off.begin(), S->src_pair_off.end() - 1);
@@ -488,14 +535,19 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_fixed, nv);
     ALLOC(S->d_tex, nv);
     ALLOC(S->d_pp, np);
+    ALLOC(S->d_pp64, (size_t)12 * np);
+    ALLOC(S->d_K64, (size_t)6 * nv);
     ALLOC(S->d_pair_acc, (size_t)kAcc * np);
-    ALLOC(S->d_pair_loss, np);
-    ALLOC(S->d_contrib, (size_t)12 * np);
     ALLOC(S->d_grad, (size_t)6 * nv);
-    ALLOC(S->d_grad_tmp, (size_t)6 * nv);
     ALLOC(S->d_loss, n_scenes);
     ALLOC(S->d_m, (size_t)6 * nv);
     ALLOC(S->d_v, (size_t)6 * nv);
+    ALLOC(S->d_bpow, 2);
+    {
+      ALLOC(S->d_qcount, 1);
+      ALLOC(S->d_qoverflow, 1);
+      ALLOC(S->d_tile_counter, 1);
+    }
     ALLOC(S->d_lambda, 1);
     ALLOC(S->d_T, (size_t)12 * nv);
     ALLOC(S->d_T_eval, (size_t)12 * nv);
@@ -535,6 +587,27 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     CK(cudaMemcpyAsync(S->d_T, I.data(), I.size() * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(S->d_m, 0, 6 * (size_t)nv * 8, st));
     CK(cudaMemsetAsync(S->d_v, 0, 6 * (size_t)nv * 8, st));
+    {
+      const double bp[2] = {o.beta1, o.beta2};
+      CK(cudaMemcpy(S->d_bpow, bp, sizeof(bp), cudaMemcpyHostToDevice));
+      std::vector<double> K64(6 * (size_t)nv);
+      int64_t vb = 0;
+      for (int s2 = 0; s2 < n_scenes; ++s2) {
+        for (int v = 0; v < descs[s2].n_views; ++v) {
+          const epo_view_desc& vd = descs[s2].views[v];
+          K64[6 * (vb + v) + 0] = vd.fx;
+          K64[6 * (vb + v) + 1] = vd.fy;
+          K64[6 * (vb + v) + 2] = vd.cx;
+          K64[6 * (vb + v) + 3] = vd.cy;
+          K64[6 * (vb + v) + 4] = 1.0 / vd.fx;
+          K64[6 * (vb + v) + 5] = 1.0 / vd.fy;
+        }
+        vb += descs[s2].n_views;
+      }
+      CK(cudaMemcpy(S->d_K64, K64.data(), K64.size() * 8, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemsetAsync(S->d_qcount, 0, 4, st));
+    CK(cudaMemsetAsync(S->d_qoverflow, 0, 4, st));
     CK(cudaMemsetAsync(S->d_step, 0, 8, st));
     CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
     CK(cudaMemsetAsync(S->d_done, 0, 4, st));
@@ -573,14 +646,13 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     }
     std::vector<unsigned long long> th(S->tex.begin(), S->tex.end());
     CK(cudaMemcpyAsync(S->d_tex, th.data(), nv * 8, cudaMemcpyHostToDevice, st));
-    if (o.timing) {
-      CK(cudaEventCreate(&S->ev0));
-      CK(cudaEventCreate(&S->ev1));
-    }
+    if (o.timing)
+      for (auto& e2 : S->ev) CK(cudaEventCreate(&e2));
     // schedule
     S->block = o.block_threads ? o.block_threads : 256;
-    S->rpt = o.records_per_thread ? o.records_per_thread : 4;
+    S->rpt = o.records_per_thread ? o.records_per_thread : 2;
     S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG;
+    if (!schedule_fits(S, S->rpt, S->block)) S->block = 128;
     epo_status bs = build_tiles(S, S->block * S->rpt);
     if (bs != EPO_OK) return bs;
     CK(cudaStreamSynchronize(st));
@@ -592,8 +664,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
 void destroy_impl(epo_scene* S) {
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
-  if (S->ev0) cudaEventDestroy(S->ev0);
-  if (S->ev1) cudaEventDestroy(S->ev1);
+  for (auto e2 : S->ev)
+    if (e2) cudaEventDestroy(e2);
   for (auto t : S->tex)
     if (t) cudaDestroyTextureObject(t);
   for (auto a : S->arrays)
@@ -721,6 +793,8 @@ epo_status epo_set_state(epo_scene_t S, int64_t step, const double* m, const dou
   else CK(cudaMemsetAsync(S->d_m, 0, 6 * (size_t)S->n_views * 8, S->stream));
   if (v) CK(cudaMemcpyAsync(S->d_v, v, 6 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
   else CK(cudaMemsetAsync(S->d_v, 0, 6 * (size_t)S->n_views * 8, S->stream));
+  const double bp[2] = {pow(S->opt.beta1, (double)(step + 1)), pow(S->opt.beta2, (double)(step + 1))};
+  CK(cudaMemcpyAsync(S->d_bpow, bp, sizeof(bp), cudaMemcpyHostToDevice, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   return EPO_OK;
 }
@@ -768,10 +842,13 @@ epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev
   if (st != EPO_OK) return st;
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, nullptr);
+  MARK(0, S->stream);
   CK(launch_pair_setup(a, MODE_FWD, S->stream));
+  MARK(1, S->stream);
   st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->stream);
   if (st != EPO_OK) return st;
-  CK(launch_finalize(a, 0, S->stream));
+  CK(launch_poses(a, 0, S->stream));
+  MARK(3, S->stream);
   CK(cudaMemcpyAsync(loss_dev, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToDevice, S->stream));
   return EPO_OK;
 }
@@ -781,10 +858,13 @@ epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* d
   if (!S || !dloss_dev || !grad_xi_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, dloss_dev);
+  MARK(0, S->stream);
   CK(launch_pair_setup(a, MODE_BWD, S->stream));
+  MARK(1, S->stream);
   epo_status st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->stream);
   if (st != EPO_OK) return st;
-  CK(launch_finalize(a, 1, S->stream));
+  CK(launch_poses(a, 1, S->stream));
+  MARK(3, S->stream);
   CK(launch_apply_left_jacobian(xi_dev, S->d_grad, grad_xi_dev, S->n_views, S->stream));
   return EPO_OK;
 }
@@ -818,11 +898,30 @@ epo_status epo_last_loss(epo_scene_t S, double* loss) {
   return EPO_OK;
 }
 
+epo_status epo_fixup_stats(epo_scene_t S, int64_t* queued, int64_t* overflow) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  unsigned int h[2] = {0u, 0u};
+  CK(cudaMemcpyAsync(&h[0], S->d_qcount, 4, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaMemcpyAsync(&h[1], S->d_qoverflow, 4, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (queued) *queued = h[0];
+  if (overflow) *overflow = h[1];
+  return EPO_OK;
+}
+
 epo_status epo_kernel_time(epo_scene_t S, float* ms) {
   if (!S || !ms) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
-  if (!S->ev0 || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
-  CK(cudaEventSynchronize(S->ev1));
-  CK(cudaEventElapsedTime(ms, S->ev0, S->ev1));
+  if (!S->ev[0] || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
+  CK(cudaEventSynchronize(S->ev[3]));
+  CK(cudaEventElapsedTime(ms, S->ev[1], S->ev[2]));
+  return EPO_OK;
+}
+
+epo_status epo_stage_times(epo_scene_t S, float* ms) {
+  if (!S || !ms) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  if (!S->ev[0] || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
+  CK(cudaEventSynchronize(S->ev[3]));
+  for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(ms + k, S->ev[k], S->ev[k + 1]));
   return EPO_OK;
 }
 
@@ -867,7 +966,7 @@ epo_status epo_autotune(epo_scene_t S) {
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   S->tuned = true;  // also guards against recursion through maybe_autotune
   const int gathers[2] = {GATHER_LDG, GATHER_TEX};
-  const int rpts[3] = {2, 4, 8};
+  const int rpts[3] = {1, 2, 4};
   const int blocks[3] = {128, 256, 512};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -879,6 +978,7 @@ epo_status epo_autotune(epo_scene_t S) {
     for (int r : rpts)
       for (int b : blocks) {
         if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
+        if (!schedule_fits(S, r, b)) continue;
         if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
         float tot = 0.f;
         for (int it = 0; it < 4; ++it) {

@@ -4,16 +4,21 @@
 //   records  : one array for all views of all scenes, view-major, raster order inside a
 //              view; 16 B {f32 u, f32 v, f32 z, 0} or 8 B {u16 u, u16 v, f16 z, 0}.
 //   map atlas: every view's distance transform field, rows padded to a 128-byte pitch,
-//              each view starting on a 512-byte boundary (so a pitched 2-D texture can
-//              alias it); f32 or bf16.
-//   views    : ViewDev table (intrinsics in f32 for the pixel math, sizes, offsets).
-//   tiles    : the persistent kernels' work list: (view, first record, count), view-major
+//              each view starting on a 512-byte boundary; f32 or bf16.  The texture path
+//              reads per-view gather-capable CUDA arrays holding the same values.
+//   views    : ViewDev table (intrinsics in f32 for the pixel math, sizes, offsets) and
+//              the f64 intrinsics (K64) for the exact re-evaluation path.
+//   tiles    : the persistent kernel's work list: (view, first record, count), view-major
 //              so that blocks running at the same time share source and target maps.
 //   pairs    : per source view a list of its outgoing pair ids (the pairs that reuse the
 //              tile's lifted records), per pair the target view; per pose a list of
 //              (pair, role) used by the deterministic FP64 gradient gather.
-//   poses    : f64 [R|t] per view, Adam moments, step counter, lambda -- all on device
-//              so that a whole optimisation step is a replayable CUDA graph.
+//   exact path: samples whose FP32 evaluation lies within its own rounding-error bound of
+//              a discontinuity (bilinear cell line, image border, depth threshold, clamp)
+//              are buffered per block in shared memory and re-evaluated with FP64
+//              decisions by the same kernel.
+//   poses    : f64 [R|t] per view, Adam moments, beta powers, step counter, lambda -- all
+//              on device so that a whole optimisation step is a replayable CUDA graph.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,32 +48,52 @@ struct TileDev {
   int64_t begin;    // first record
 };
 
-// Relative pose T_ji = T_j T_i^-1 rounded to f32 for the pixel math (a1), one per pair.
-struct PairParam {
+// Everything the edge kernel needs for one pair i -> j, built by the pair setup (a1):
+// the relative pose T_ji = T_j T_i^-1 rounded to f32, the target's intrinsics and map,
+// and the pair constants of the FP32 rounding-error bound.  128 bytes, read with eight
+// uniform 16-byte loads per pair.
+struct alignas(16) PairParam {
   float r[9];
   float t[3];
+  float fx, fy, cx, cy;   // target intrinsics (f32)
+  float hw, hh;           // (W-1)/2, (H-1)/2: the valid range is |u' - hw| <= hw
+  float Et;               // rounding bound of Y from the rounded translation
+  float fx2, fy2;         // 2 fx, 2 fy (bound scale with a 2x safety factor)
+  float cu, cv;           // rounding of u', v' themselves
+  int32_t W, H, pitch;    // target map
+  int64_t map_off;
+  unsigned long long tex; // texture object of the target map
 };
+static_assert(sizeof(PairParam) == 128, "PairParam layout");
 
 struct EdgeArgs {
   const void* rec;
   const void* map;
   const ViewDev* views;
+  const double* K64;             // n_views x 6 (fx, fy, cx, cy, 1/fx, 1/fy) in f64
   const TileDev* tiles;
   int32_t n_tiles;
   const int32_t* src_pair_off;   // n_views + 1
   const int32_t* src_pair_ids;   // pairs grouped by source view
+  const int32_t* pair_src;       // n_pairs
   const int32_t* pair_dst;       // n_pairs
   const PairParam* pp;           // n_pairs
+  const double* pp64;            // n_pairs x 12: R_ji (9), t_ji (3) in f64
   const uint8_t* pair_active;    // n_pairs
   const unsigned long long* tex; // n_views texture objects (GATHER_TEX)
   double* pair_acc;              // n_pairs x kAcc
   const double* lambda;          // device scalar
+  unsigned int* q_count;         // samples re-evaluated on the exact path this evaluation
+  unsigned int* q_overflow;      // samples that found the block buffer full (FP32 decisions)
+  int* tile_counter;             // dynamic work distribution, reset by the pair setup
+  int32_t max_pairs;             // most outgoing pairs of any view (shared accumulators)
   float delta;
   float eps_z;
 };
 
 struct StepArgs {
   int32_t n_views, n_pairs, n_scenes;
+  const unsigned long long* tex;     // n_views texture objects (copied into PairParam)
   const int32_t* pair_src;
   const int32_t* pair_dst;
   const int32_t* pair_scene;
@@ -82,20 +107,23 @@ struct StepArgs {
   const double* T;                   // poses used by the evaluation (n_views x 12)
   double* T_store;                   // poses updated by the retraction
   PairParam* pp;
+  double* pp64;
   double* pair_acc;
-  double* pair_loss;                 // n_pairs
-  double* contrib;                   // n_pairs x 12 (target part, source part)
   double* grad;                      // n_views x 6
   double* loss;                      // n_scenes
   double* m;                         // Adam moments
   double* v;
+  double* bpow;                      // beta1^(s+1), beta2^(s+1) for the next step s
   int64_t* step;
   double* lambda;
   int32_t* flag;                     // bit 0: non-finite loss/gradient
-  unsigned int* done;                // retraction completion counter
+  unsigned int* done;                // completion counter of the pose kernel
+  unsigned int* q_count;             // exact-path sample counter, reset by the pair setup
+  int* tile_counter;                 // edge-kernel work counter, reset by the pair setup
   const double* gscale;              // per-scene scale of the gradient (NULL = 1)
   double lambda0, lambda1;
   int32_t lambda_steps;
+  double inv_lambda_steps;
   int32_t norm_all;
   double lr_rot, lr_trans, beta1, beta2, adam_eps;
 };
@@ -104,8 +132,8 @@ struct StepArgs {
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_edge(const EdgeArgs& a, int mode, int rec_dtype, int map_dtype, int gather,
                         int rpt, int block, int grid, cudaStream_t s);
-cudaError_t launch_finalize(const StepArgs& a, int with_grad, cudaStream_t s);
-cudaError_t launch_retract(const StepArgs& a, cudaStream_t s);
+// pose kernel: with_grad 0 = loss only, 1 = loss + gradient, 2 = + Adam/Exp update
+cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s);
 cudaError_t launch_twist_poses(const double* T, const double* xi, double* T_out, int n,
                                cudaStream_t s);
 cudaError_t launch_apply_left_jacobian(const double* xi, const double* g, double* out, int n,
@@ -114,5 +142,7 @@ cudaError_t launch_map_check(const void* map, int dtype, int64_t n, int32_t* bad
 cudaError_t launch_edt(const uint8_t* edges, int W, int H, float* map, cudaStream_t s);
 cudaError_t launch_round_bf16(const float* src, uint16_t* dst, int64_t n, cudaStream_t s);
 int edt_max_height();
+const void* edge_kernel_ptr(int mode, int rec_dtype, int map_dtype, int gather, int rpt);
+size_t edge_smem_bytes(int rpt, int block, int max_pairs);
 
 }  // namespace epo

@@ -6,9 +6,11 @@ Tolerances (FP32 path, stated by the arithmetic):
     coordinate (<= 5e-5 px at 518 px); with |grad DTF| <= 1 the per-sample distance moves by
     the same amount, which averages to ~1e-6 relative over thousands of samples.
   * n_valid per pair is an integer decided by FP comparisons of the projected position
-    against the image border (and the depth against eps_z).  The kernel decides in FP32, the
-    oracle in FP64; they may differ only on samples the oracle finds within 1e-3 px of a
-    border (its pair_near count), so |n_gpu - n_oracle| <= near is required exactly.
+    against the image border (and the depth against eps_z).  The kernel takes every decision
+    that its FP32 rounding-error bound cannot settle (border, bilinear cell, depth threshold,
+    clamp) again in FP64, so it decides as an FP64 evaluation does; the two FP64 evaluations
+    may still differ on samples within FP64 rounding of a boundary (the oracle's pair_near
+    count at a 1e-9 px margin), so |n_gpu - n_oracle| <= near is required exactly.
   * BF16 maps / FP16 depth: against the oracle fed the same rounded values ("kernel parity")
     the FP32 tolerances hold; against the oracle fed the full-precision inputs ("precision
     cost") loss and gradient agree to 1e-2.
@@ -35,7 +37,7 @@ LOSS_RTOL = 1e-5
 GRAD_RTOL = 1e-4
 PAIR_RHO_RTOL = 1e-5
 PAIR_GRAD_RTOL = 1e-4
-CELL_FLIPS = 4  # adjacent-cell choices per pair allowed between FP32 and FP64 (see module doc)
+CELL_FLIPS = 0  # adjacent-cell choices per pair allowed to differ (none: the kernel re-decides them in FP64)
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +69,8 @@ def allowances(o, pairs, T, n_views, lam, delta):
     sample in or out of a pair's mean: the pair loss moves by at most (H(lambda) + l_p)/n and
     the pair's gradient by at most one sample's term plus a 1/n rescale.  Independently, a
     sample within ~1e-4 px of a bilinear cell line may take the neighbouring cell, changing
-    its slope term by at most twice its size; CELL_FLIPS such samples are allowed per pair.
+    its slope term by at most twice its size; CELL_FLIPS such samples are allowed per pair
+    (zero: the kernel settles every cell choice within its FP32 error bound in FP64).
     The target pose receives a pair's 6-vector as is, the source pose through -Ad(T_ji)^T,
     whose norm is at most 2 + |t_ji|."""
     near = o["pair_near"].astype(float)
@@ -111,7 +114,7 @@ def check_against_oracle(loss_g, grad_g, o, pairs, T, lam=10.0, delta=1.0, stats
 
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("gather", [epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX])
-@pytest.mark.parametrize("rpt,block", [(4, 256), (2, 128), (8, 512)])
+@pytest.mark.parametrize("rpt,block", [(4, 256), (2, 128), (1, 512)])
 def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
     sc, maps = ring8
     s = gpu_scene(sc, maps, gather=gather, records_per_thread=rpt, block_threads=block)
@@ -125,7 +128,7 @@ def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
 def test_gather_paths_and_schedules_agree(ring8):
     sc, maps = ring8
     res = []
-    for gather, rpt, block in [(1, 4, 256), (2, 4, 256), (1, 8, 128), (2, 2, 512)]:
+    for gather, rpt, block in [(1, 4, 256), (2, 4, 256), (1, 1, 128), (2, 2, 512)]:
         s = gpu_scene(sc, maps, gather=gather, records_per_thread=rpt, block_threads=block)
         s.set_poses(sc.T_init)
         res.append(s.loss_and_grad())
@@ -403,7 +406,7 @@ def test_autotune_keeps_results(ring8):
     o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
     check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=s.pair_stats())
     i = s.info()
-    assert i.records_per_thread in (2, 4, 8) and i.block_threads in (128, 256, 512)
+    assert i.records_per_thread in (1, 2, 4) and i.block_threads in (128, 256, 512)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -441,3 +444,6 @@ def test_full_size_sampled_pairs_match_oracle(ring32):
     # the whole loss and gradient (the oracle runs all 256 pairs once)
     full = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
     check_against_oracle(loss[0], grad, full, sc.pairs, sc.T_init, stats=st)
+    # a fraction of a percent of the samples took the exact path; none overflowed its queue
+    queued, overflow = epo._binding.epo_fixup_stats(s.handle)
+    assert 0 < queued < 0.05 * s.info().evals_per_step and overflow == 0
