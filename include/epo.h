@@ -55,7 +55,8 @@ typedef enum {
   EPO_ERR_OOM = 3,         /* device allocation failed */
   EPO_ERR_NUMERIC = 4,     /* non-finite loss or gradient; the pose update was refused */
   EPO_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
-  EPO_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+  EPO_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
+  EPO_ERR_TOO_LARGE = 7    /* the problem exceeds a fixed capacity (epo_loss_and_grad_noalloc) */
 } epo_status;
 
 enum { EPO_F32 = 0, EPO_F16 = 1, EPO_BF16 = 2 };
@@ -242,6 +243,64 @@ epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, fl
                               void* cuda_stream);
 /* Round n floats to bfloat16 (round to nearest even), device buffers. */
 epo_status epo_round_bf16(const float* src_dev, uint16_t* dst_dev, int64_t n, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Loss and gradient without any device allocation.
+ *
+ * This entry point has no counterpart in the paper.  It exists for callers
+ * that cannot call cudaMalloc: a host application that owns every byte of
+ * device memory (a plugin running inside another engine, a fixed memory
+ * budget handed out up front), a real-time loop in which an allocation may
+ * block or fail, or code that runs while the device allocator is off limits.
+ * Such a caller keeps its inputs and outputs in its own device buffers and
+ * passes them in; no scene handle is created.
+ *
+ * It computes what epo_loss_and_grad_dev computes (Eqs. 6-8 and the
+ * left-perturbation pose gradient, EPO_F32 records and FP32 maps) for one
+ * scene, with every projection and branch decision taken in FP64.  The
+ * intermediate per-pair sums live in one file-scope device array of the
+ * library of fixed size, about 0.9 MB, which every GPU that loads the
+ * library reserves until the process exits.  Hence the limits below:
+ * larger problems are rejected with EPO_ERR_TOO_LARGE before any work.
+ *
+ *   - The first call on a device looks up that array's device address (with
+ *     the device current) and keeps it; make that first call before any
+ *     stream capture.
+ *   - Every call reuses the same array and clears what must start at zero;
+ *     calls that overlap on the GPU (another stream, another host thread)
+ *     race on it and give wrong results.  Order them on one stream.
+ *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating
+ *     library routine, on the device or the host.
+ *   - Stream-ordered on cuda_stream; it does not synchronise.  Status codes:
+ *     EPO_ERR_INVALID_ARG for a NULL pointer, no view or pair, or an invalid
+ *     lambda / huber_delta / eps_z / norm_mode; EPO_ERR_TOO_LARGE beyond the
+ *     limits; EPO_ERR_CUDA if a launch fails.  Indices and sizes inside the
+ *     device buffers are not checked: they must be consistent.
+ * ------------------------------------------------------------------------ */
+#define EPO_NOALLOC_MAX_VIEWS 1024
+#define EPO_NOALLOC_MAX_PAIRS 4096
+
+typedef struct {
+  int32_t n_views, n_pairs;      /* 1..EPO_NOALLOC_MAX_VIEWS, 1..EPO_NOALLOC_MAX_PAIRS */
+  const float* records;          /* device, 16-byte aligned: {u, v, z, 0} per record, z > 0 finite */
+  const int64_t* rec_off;        /* device: n_views + 1 record offsets, view-major */
+  int64_t max_records_per_view;  /* host value: the largest rec_off[i+1] - rec_off[i] */
+  const float* maps;             /* device: every view's map, H rows of W floats, dense */
+  const int64_t* map_off;        /* device: n_views offsets (in floats) into maps */
+  const int32_t* W;              /* device: n_views map widths (>= 2) */
+  const int32_t* H;              /* device: n_views map heights (>= 2) */
+  const double* K;               /* device: n_views x 4 intrinsics (fx, fy, cx, cy) */
+  const int32_t* pairs;          /* device: 2 x n_pairs directed pairs (i, j) */
+  const double* T;               /* device: n_views x 12 poses [R|t], world -> camera */
+  double lambda;                 /* clamp of the distance (Eq. 7) */
+  double huber_delta;
+  double eps_z;
+  int32_t norm_mode;             /* EPO_NORM_VALID | EPO_NORM_ALL */
+} epo_noalloc_problem;
+
+/* loss_dev: 1 double (device); grad_dev: n_views x 6 doubles (device). */
+epo_status epo_loss_and_grad_noalloc(const epo_noalloc_problem* problem, double* loss_dev,
+                                     double* grad_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

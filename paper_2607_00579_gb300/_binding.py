@@ -19,8 +19,12 @@ EPO_ERR_OOM = 3
 EPO_ERR_NUMERIC = 4
 EPO_ERR_TIMEOUT = 5
 EPO_ERR_INTERNAL = 6
+EPO_ERR_TOO_LARGE = 7
 STATUS_NAMES = {0: "EPO_OK", 1: "EPO_ERR_INVALID_ARG", 2: "EPO_ERR_CUDA", 3: "EPO_ERR_OOM",
-                4: "EPO_ERR_NUMERIC", 5: "EPO_ERR_TIMEOUT", 6: "EPO_ERR_INTERNAL"}
+                4: "EPO_ERR_NUMERIC", 5: "EPO_ERR_TIMEOUT", 6: "EPO_ERR_INTERNAL",
+                7: "EPO_ERR_TOO_LARGE"}
+EPO_NOALLOC_MAX_VIEWS = 1024
+EPO_NOALLOC_MAX_PAIRS = 4096
 
 EPO_F32, EPO_F16, EPO_BF16 = 0, 1, 2
 EPO_NORM_VALID, EPO_NORM_ALL = 0, 1
@@ -34,6 +38,7 @@ EXPORTED = [
     "epo_loss_and_grad_dev", "epo_pair_stats", "epo_forward_dev", "epo_backward_dev", "epo_step",
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
+    "epo_loss_and_grad_noalloc",
 ]
 
 
@@ -75,6 +80,15 @@ class epo_scene_info(ctypes.Structure):
                 ("n_tiles", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32)]
+
+
+class epo_noalloc_problem(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int32), ("n_pairs", ctypes.c_int32), ("records", ctypes.c_void_p),
+                ("rec_off", ctypes.c_void_p), ("max_records_per_view", ctypes.c_int64),
+                ("maps", ctypes.c_void_p), ("map_off", ctypes.c_void_p), ("W", ctypes.c_void_p),
+                ("H", ctypes.c_void_p), ("K", ctypes.c_void_p), ("pairs", ctypes.c_void_p),
+                ("T", ctypes.c_void_p), ("lam", ctypes.c_double), ("huber_delta", ctypes.c_double),
+                ("eps_z", ctypes.c_double), ("norm_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -126,6 +140,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "epo_kernel_time": (I32, [S, ctypes.POINTER(ctypes.c_float)]),
         "epo_fixup_stats": (I32, [S, P, P]),
         "epo_stage_times": (I32, [S, P]),
+        "epo_loss_and_grad_noalloc": (I32, [ctypes.POINTER(epo_noalloc_problem), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -242,6 +257,12 @@ def epo_set_pair_subset(scene, ids):
     import numpy as np
     a = np.ascontiguousarray(ids, dtype=np.int32) if ids is not None and len(ids) else None
     _call("epo_set_pair_subset", scene, ctypes.c_int32(0 if a is None else len(a)), _ptr(a))
+
+
+def epo_loss_and_grad_noalloc(problem, loss_dev, grad_dev, stream: int = 0) -> int:
+    """Returns the status code (the caller decides how to report it)."""
+    return load().epo_loss_and_grad_noalloc(ctypes.byref(problem), _ptr(loss_dev), _ptr(grad_dev),
+                                            ctypes.c_void_p(stream))
 
 
 def epo_distance_field(edges_dev, W: int, H: int, map_dev, stream: int = 0):
