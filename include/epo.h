@@ -100,7 +100,8 @@ typedef struct {
   int32_t norm_mode;         /* EPO_NORM_VALID | EPO_NORM_ALL */
   double lr_rot, lr_trans;   /* Adam step sizes for omega and upsilon */
   double beta1, beta2, adam_eps; /* Adam moments (Section 3: 0.9, 0.999) */
-  int32_t autotune;          /* 1: pick the kernel schedule by timing on first use */
+  int32_t autotune;          /* 1: pick the kernel schedule by timing on first use;
+                                2: the same, each timed launch starting from a cold L2 */
   int32_t gather;            /* EPO_GATHER_* (AUTO = LDG unless autotuned) */
   int32_t block_threads;     /* 0 = default (256); else 64..512, multiple of 32 */
   int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 */
@@ -118,6 +119,7 @@ typedef struct {
   int64_t record_bytes, map_bytes;
   int32_t n_tiles;           /* work items of the persistent kernels */
   int32_t gather, block_threads, records_per_thread, grid_blocks; /* schedule in use */
+  int32_t kernels_per_step;  /* kernel launches in one epo_step */
 } epo_scene_info;
 
 /* Defaults: delta 1, lambda 10 -> 6 over 1000 steps, eps_z 1e-6, NORM_VALID,
@@ -231,7 +233,9 @@ epo_status epo_stage_times(epo_scene_t scene, float* ms);
 epo_status epo_set_pair_subset(epo_scene_t scene, int32_t n, const int32_t* pair_ids);
 
 /* Time the kernel schedules on the current poses and keep the fastest
- * (block size, records per thread, gather path). */
+ * (block size, records per thread, gather path).  With options.autotune == 2
+ * each timed launch starts from a cold L2; a temporary scratch buffer of
+ * twice the L2 size is allocated for that during the call. */
 epo_status epo_autotune(epo_scene_t scene);
 
 /* Distance transform field (Algorithm 1, ComputeDistanceFields): exact

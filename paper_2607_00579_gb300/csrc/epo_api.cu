@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -312,7 +313,8 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
   return EPO_OK;
 }
 
-// One optimisation step (a1 .. a9): four kernels, no host synchronisation.
+// One optimisation step (a1 .. a9): pair setup, edge kernel, pose kernel; no host
+// synchronisation.
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   StepArgs a = step_args(S, S->d_T, nullptr);
   MARK(0, s);
@@ -746,6 +748,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
+  info->kernels_per_step = 3;
   return EPO_OK;
 }
 
@@ -972,6 +975,17 @@ epo_status epo_autotune(epo_scene_t S) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   StepArgs a = step_args(S, S->d_T, nullptr);
+  // autotune == 2: every timed launch starts from a cold L2 (a scratch buffer twice the
+  // L2 size is written, then half of it read back, before each launch)
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  if (S->opt.autotune == 2) {
+    int dev = 0, l2 = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    flush_bytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20);
+    CK(cudaMalloc(&flush, flush_bytes + 16));
+  }
   float best = 1e30f;
   int bg = S->gather, br = S->rpt, bb = S->block;
   for (int g : gathers)
@@ -982,6 +996,11 @@ epo_status epo_autotune(epo_scene_t S) {
         if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
         float tot = 0.f;
         for (int it = 0; it < 4; ++it) {
+          if (flush) {
+            CK(cudaMemsetAsync(flush, it + 1, flush_bytes, S->stream));
+            CK(launch_l2_read(flush, (int64_t)flush_bytes / 2, (unsigned*)((char*)flush + flush_bytes),
+                              S->sm_count, S->stream));
+          }
           CK(launch_pair_setup(a, MODE_FUSED, S->stream));
           CK(cudaEventRecord(e0, S->stream));
           epo_status st = run_edge(S, MODE_FUSED, g, r, b, S->stream);
@@ -999,6 +1018,10 @@ epo_status epo_autotune(epo_scene_t S) {
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (flush) {
+    CK(cudaStreamSynchronize(S->stream));
+    CK(cudaFree(flush));
+  }
   S->gather = bg;
   S->rpt = br;
   S->block = bb;

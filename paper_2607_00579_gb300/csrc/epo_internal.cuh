@@ -130,6 +130,7 @@ struct StepArgs {
 
 // ---- launchers (epo_kernels.cu) ----
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);
 cudaError_t launch_edge(const EdgeArgs& a, int mode, int rec_dtype, int map_dtype, int gather,
                         int rpt, int block, int grid, cudaStream_t s);
 // pose kernel: with_grad 0 = loss only, 1 = loss + gradient, 2 = + Adam/Exp update
