@@ -208,7 +208,7 @@ struct AmbEntry {
   float u, v, z;
   int p;
 };
-constexpr int kAmbCap = 1024;  // entries per block; re-evaluated once more than half full
+constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
 
 // The exact path: lift, transform and project in FP64, take the validity, cell and clamp
 // decisions in FP64 (so the branch is the one an FP64 evaluation takes); the value and the
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   float4* s_X = s_dyn;                                                    // [blockDim * RPT]
   float2* s_UV = reinterpret_cast<float2*>(s_dyn + blockDim.x * RPT);    // [blockDim * RPT]
   float* s_part = reinterpret_cast<float*>(s_UV + blockDim.x * RPT);     // [warps][max_pairs][8]
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_next;
   __shared__ int s_amb_n;
   __shared__ AmbEntry s_amb[kAmbCap];
   const int lane = threadIdx.x & 31;
@@ -297,6 +297,8 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   __syncthreads();
   while (s_tile < a.n_tiles) {
     const int t = s_tile;
+    // claim the next tile now: the atomic's round trip overlaps this tile's work
+    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_counter, 1);
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
     // a2: stream the tile's records (coalesced 128-bit loads), lift once per record into
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       for (int w = 0; w < nwarp; ++w) s += s_part[((size_t)w * a.max_pairs + qq) * kAcc + slot];
       if (s != 0.f) atomicAdd(a.pair_acc + (size_t)kAcc * p + slot, (double)s);
     }
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1);
+    if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
     // exact path: when the buffer is more than half full, and once more before exiting
     const int n_amb = min(s_amb_n, kAmbCap);
@@ -483,6 +485,19 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // an FP64 warp instruction occupies its sub-partition's FP64 pipe for many cycles.
 constexpr int kPoseThreads = 128;
 constexpr int kPosesPerBlock = kPoseThreads / 16;
+
+// Taylor coefficients (in theta^2) of A = sin(t)/t, B = (1 - cos t)/t^2, C = (t - sin t)/t^3
+__device__ constexpr double kExpA[5] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0};
+__device__ constexpr double kExpB[5] = {0.5, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0};
+__device__ constexpr double kExpC[5] = {1.0 / 6.0, -1.0 / 120.0, 1.0 / 5040.0, -1.0 / 362880.0, 1.0 / 39916800.0};
+
+// Entry (r, c) of [w]x = [[0, -w2, w1], [w2, 0, -w0], [-w1, w0, 0]] with runtime r, c.
+__device__ __forceinline__ double cross_entry(int r, int c, double w0, double w1, double w2) {
+  if (r == c) return 0.0;
+  const int k = 3 - r - c;
+  const double wk = k == 0 ? w0 : (k == 1 ? w1 : w2);
+  return ((c - r + 3) % 3) == 1 ? -wk : wk;
+}
 
 __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_grad, int n_pose_blocks) {
   __shared__ double s_sum[kPoseThreads];
@@ -559,45 +574,50 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       double x[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) x[k] = __shfl_sync(0xffffffffu, xi, base + k);
-      double Tnew = 0.0;
-      if (!skip && e < 12) {
-        const int r = e >> 2, c = e & 3;
-        const double w0 = x[3], w1 = x[4], w2 = x[5];
-        const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-        double A, B, C;
-        if (th2 < 2.5e-3) {  // theta < 0.05: series, truncation below 1e-17
-          // Horner forms of the Taylor series; constant reciprocals keep the FP64 pipe free
-          // of divisions
-          constexpr double r6 = 1.0 / 6.0, r12 = 1.0 / 12.0, r20 = 1.0 / 20.0, r30 = 1.0 / 30.0;
-          constexpr double r42 = 1.0 / 42.0, r56 = 1.0 / 56.0, r72 = 1.0 / 72.0, r90 = 1.0 / 90.0;
-          constexpr double r110 = 1.0 / 110.0;
-          A = 1.0 - th2 * r6 * (1.0 - th2 * r20 * (1.0 - th2 * r42 * (1.0 - th2 * r72)));
-          B = 0.5 * (1.0 - th2 * r12 * (1.0 - th2 * r30 * (1.0 - th2 * r56 * (1.0 - th2 * r90))));
-          C = r6 * (1.0 - th2 * r20 * (1.0 - th2 * r42 * (1.0 - th2 * r72 * (1.0 - th2 * r110))));
-        } else {
-          const double th = sqrt(th2);
-          double sn, cs;
-          sincos(th, &sn, &cs);
-          A = sn / th;
-          B = (1.0 - cs) / th2;
-          C = (th - sn) / (th2 * th);
-        }
-        const double w[3] = {w0, w1, w2};
-        // row r of W = [w]x and of W^2 = w w^T - th2 I
-        const double Wr[3] = {r == 0 ? 0.0 : (r == 1 ? w2 : -w1), r == 0 ? -w2 : (r == 1 ? 0.0 : w0),
-                              r == 0 ? w1 : (r == 1 ? -w0 : 0.0)};
-        double Er[4];
-        double tr = 0.0;
+      // lane e = 4r + c of the group forms entry (r, c) of Exp(xi) = [E_R | E_t]; the rows
+      // are then exchanged by shuffles for the composition T <- Exp(xi) T
+      const int r = (e >> 2) < 3 ? (e >> 2) : 2, c = e & 3;
+      const double w0 = x[3], w1 = x[4], w2 = x[5];
+      const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+      double A, B, C;
+      if (th2 < 2.5e-3) {
+        // theta < 0.05: Taylor polynomials in theta^2, truncation below 1e-20
+        A = fma(th2, fma(th2, fma(th2, fma(th2, kExpA[4], kExpA[3]), kExpA[2]), kExpA[1]), kExpA[0]);
+        B = fma(th2, fma(th2, fma(th2, fma(th2, kExpB[4], kExpB[3]), kExpB[2]), kExpB[1]), kExpB[0]);
+        C = fma(th2, fma(th2, fma(th2, fma(th2, kExpC[4], kExpC[3]), kExpC[2]), kExpC[1]), kExpC[0]);
+      } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / th2;
+        C = (th - sn) / (th2 * th);
+      }
+      const double wr = r == 0 ? w0 : (r == 1 ? w1 : w2);
+      double Erc;
+      if (c < 3) {
+        const double wc = c == 0 ? w0 : (c == 1 ? w1 : w2);
+        const double I = r == c ? 1.0 : 0.0;
+        Erc = I + A * cross_entry(r, c, w0, w1, w2) + B * (wr * wc - I * th2);
+      } else {
+        // translation: (I + B W + C W^2) upsilon, row r
+        Erc = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+          const double wk = k == 0 ? w0 : (k == 1 ? w1 : w2);
           const double I = r == k ? 1.0 : 0.0;
-          const double W2 = w[r] * w[k] - (r == k ? th2 : 0.0);
-          Er[k] = I + A * Wr[k] + B * W2;
-          tr += (I + B * Wr[k] + C * W2) * x[k];
+          Erc = fma(I + B * cross_entry(r, k, w0, w1, w2) + C * (wr * wk - I * th2), x[k], Erc);
         }
-        Er[3] = tr;
+      }
+      const int rb = base + (e & 12);
+      const double E0 = __shfl_sync(0xffffffffu, Erc, rb);
+      const double E1 = __shfl_sync(0xffffffffu, Erc, rb + 1);
+      const double E2 = __shfl_sync(0xffffffffu, Erc, rb + 2);
+      const double E3 = __shfl_sync(0xffffffffu, Erc, rb + 3);
+      double Tnew = 0.0;
+      if (!skip && e < 12) {
         const double* T = a.T_store + 12 * (size_t)v;
-        Tnew = Er[0] * T[c] + Er[1] * T[4 + c] + Er[2] * T[8 + c] + (c == 3 ? Er[3] : 0.0);
+        Tnew = fma(E0, T[c], fma(E1, T[4 + c], fma(E2, T[8 + c], c == 3 ? E3 : 0.0)));
       }
       __syncwarp();  // every lane has read the old pose before any lane writes it
       if (!skip && e < 12) a.T_store[12 * (size_t)v + e] = Tnew;
