@@ -104,7 +104,7 @@ typedef struct {
                                 2: the same, each timed launch starting from a cold L2 */
   int32_t gather;            /* EPO_GATHER_* (AUTO = LDG unless autotuned) */
   int32_t block_threads;     /* 0 = default (256); else 64..512, multiple of 32 */
-  int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 */
+  int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 (two in flight at a time) */
   int32_t grid_blocks;       /* 0 = default (persistent: SMs x resident blocks) */
   int32_t timing;            /* 1: bracket the edge kernel with CUDA events (epo_kernel_time) */
 } epo_options;

@@ -325,120 +325,126 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       float acc[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-      // phase A: project every sample and take the decisions the FP32 bound allows
-      float Y0[RPT], Y1[RPT], Y2[RPT], iz[RPT], up[RPT], vp[RPT], tu[RPT], tv[RPT];
-      bool ok[RPT], amb[RPT];
-      int x0[RPT], y0[RPT];
+      // the thread's RPT records, ILP of them in flight at a time: one reduction per pair
+      // for all RPT samples, registers for only ILP
+      constexpr int ILP = RPT < 2 ? RPT : 2;
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const float4 X = s_X[threadIdx.x + r * blockDim.x];
-        Y0[r] = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
-        Y1[r] = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
-        Y2[r] = fmaf(P.r[6], X.x, fmaf(P.r[7], X.y, fmaf(P.r[8], X.z, P.t[2])));
-        const float E = X.w + P.Et;  // |Y_k - Y_k(exact)| <= E
-        const bool front = (X.w >= 0.f) && (Y2[r] > eps_z - E);
-        iz[r] = front ? rcp_approx(Y2[r]) : 0.f;
-        const float xn = Y0[r] * iz[r], yn = Y1[r] * iz[r];
-        up[r] = fmaf(P.fx, xn, P.cx);
-        vp[r] = fmaf(P.fy, yn, P.cy);
-        const float Eiz = E * iz[r];
-        tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn), Eiz), P.cu);  // bound on |u' - u'(exact)|
-        tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn), Eiz), P.cv);
-        const bool cand = front && (fabsf(up[r] - P.hw) <= P.hw + tu[r]) && (fabsf(vp[r] - P.hh) <= P.hh + tv[r]);
-        // within the bound of an integer coordinate (cell lines and the border are integers)
-        // or of the depth threshold: the branch taken must come from the exact evaluation
-        amb[r] = cand && (fabsf(up[r] - rintf(up[r])) <= tu[r] || fabsf(vp[r] - rintf(vp[r])) <= tv[r] ||
-                          fabsf(Y2[r] - eps_z) <= E);
-        ok[r] = cand && !amb[r];
-        // cell of a valid sample: ok implies tu < u' < W-1-tu, so floor(u') is in [0, W-2];
-        // the unsigned range check keeps every gather inside the map regardless
-        x0[r] = __float2int_rd(up[r]);
-        y0[r] = __float2int_rd(vp[r]);
-        if (ok[r] && !((unsigned)x0[r] <= (unsigned)(P.W - 2) && (unsigned)y0[r] <= (unsigned)(P.H - 2))) {
-          ok[r] = false;
-          amb[r] = true;
-        }
-      }
-      // phase B: all gathers in flight together
-      float m00[RPT], m01[RPT], m10[RPT], m11[RPT];
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        if (ok[r]) {
-          taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, x0[r], y0[r], m00[r], m01[r], m10[r], m11[r]);
-        } else {
-          m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
-        }
-      }
-      // phase C: bilinear value and slope, clamp, robust penalty, adjoint
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const float ca = up[r] - (float)x0[r];
-        const float cb = vp[r] - (float)y0[r];
-        const float top = fmaf(ca, m01[r] - m00[r], m00[r]);
-        const float bot = fmaf(ca, m11[r] - m10[r], m10[r]);
-        float d = fmaf(cb, bot - top, top);
-        float ddu = fmaf(cb, (m11[r] - m10[r]) - (m01[r] - m00[r]), m01[r] - m00[r]);
-        float ddv = bot - top;
-        if (ok[r]) {
-          // the clamp is a discontinuity of the slope term: same treatment
-          const float td = fmaf(tu[r], fabsf(ddu), fmaf(tv[r], fabsf(ddv), 8.f * kU32 * (fabsf(d) + 1.f)));
-          if (fabsf(d - lam) <= td) {
+      for (int g = 0; g < RPT; g += ILP) {
+        // phase A: project every sample and take the decisions the FP32 bound allows
+        float Y0[ILP], Y1[ILP], Y2[ILP], iz[ILP], up[ILP], vp[ILP], tu[ILP], tv[ILP];
+        bool ok[ILP], amb[ILP];
+        int x0[ILP], y0[ILP];
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
+          Y0[r] = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
+          Y1[r] = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
+          Y2[r] = fmaf(P.r[6], X.x, fmaf(P.r[7], X.y, fmaf(P.r[8], X.z, P.t[2])));
+          const float E = X.w + P.Et;  // |Y_k - Y_k(exact)| <= E
+          const bool front = (X.w >= 0.f) && (Y2[r] > eps_z - E);
+          iz[r] = front ? rcp_approx(Y2[r]) : 0.f;
+          const float xn = Y0[r] * iz[r], yn = Y1[r] * iz[r];
+          up[r] = fmaf(P.fx, xn, P.cx);
+          vp[r] = fmaf(P.fy, yn, P.cy);
+          const float Eiz = E * iz[r];
+          tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn), Eiz), P.cu);  // bound on |u' - u'(exact)|
+          tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn), Eiz), P.cv);
+          const bool cand = front && (fabsf(up[r] - P.hw) <= P.hw + tu[r]) && (fabsf(vp[r] - P.hh) <= P.hh + tv[r]);
+          // within the bound of an integer coordinate (cell lines and the border are integers)
+          // or of the depth threshold: the branch taken must come from the exact evaluation
+          amb[r] = cand && (fabsf(up[r] - rintf(up[r])) <= tu[r] || fabsf(vp[r] - rintf(vp[r])) <= tv[r] ||
+                            fabsf(Y2[r] - eps_z) <= E);
+          ok[r] = cand && !amb[r];
+          // cell of a valid sample: ok implies tu < u' < W-1-tu, so floor(u') is in [0, W-2];
+          // the unsigned range check keeps every gather inside the map regardless
+          x0[r] = __float2int_rd(up[r]);
+          y0[r] = __float2int_rd(vp[r]);
+          if (ok[r] && !((unsigned)x0[r] <= (unsigned)(P.W - 2) && (unsigned)y0[r] <= (unsigned)(P.H - 2))) {
             ok[r] = false;
             amb[r] = true;
           }
         }
-        // keep the ambiguous samples for the exact path (warp-aggregated append)
-        const unsigned bal = __ballot_sync(0xffffffffu, amb[r]);
-        if (bal) {
-          const int leader = __ffs(bal) - 1;
-          int base = 0;
-          if (lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (amb[r]) {
-            const int pos = base + __popc(bal & lanemask_lt);
-            if (pos < kAmbCap) {
-              const int li = threadIdx.x + r * blockDim.x;
-              const float2 uv = s_UV[li];
-              s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
-            } else {
-              // buffer full: evaluate this sample with FP32 decisions instead
-              atomicAdd(a.q_overflow, 1u);
-              ok[r] = (Y2[r] > eps_z) && (up[r] >= 0.f) && (up[r] <= Wm1) && (vp[r] >= 0.f) && (vp[r] <= Hm1);
-              if (ok[r]) {
-                const int fx0 = min(max(x0[r], 0), P.W - 2), fy0 = min(max(y0[r], 0), P.H - 2);
-                const float fa = up[r] - (float)fx0, fb = vp[r] - (float)fy0;
-                float n00, n01, n10, n11;
-                taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, fx0, fy0, n00, n01, n10, n11);
-                const float t2 = fmaf(fa, n01 - n00, n00);
-                const float b2 = fmaf(fa, n11 - n10, n10);
-                d = fmaf(fb, b2 - t2, t2);
-                ddu = fmaf(fb, (n11 - n10) - (n01 - n00), n01 - n00);
-                ddv = b2 - t2;
+        // phase B: all gathers in flight together
+        float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          if (ok[r]) {
+            taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, x0[r], y0[r], m00[r], m01[r], m10[r], m11[r]);
+          } else {
+            m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
+          }
+        }
+        // phase C: bilinear value and slope, clamp, robust penalty, adjoint
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float ca = up[r] - (float)x0[r];
+          const float cb = vp[r] - (float)y0[r];
+          const float top = fmaf(ca, m01[r] - m00[r], m00[r]);
+          const float bot = fmaf(ca, m11[r] - m10[r], m10[r]);
+          float d = fmaf(cb, bot - top, top);
+          float ddu = fmaf(cb, (m11[r] - m10[r]) - (m01[r] - m00[r]), m01[r] - m00[r]);
+          float ddv = bot - top;
+          if (ok[r]) {
+            // the clamp is a discontinuity of the slope term: same treatment
+            const float td = fmaf(tu[r], fabsf(ddu), fmaf(tv[r], fabsf(ddv), 8.f * kU32 * (fabsf(d) + 1.f)));
+            if (fabsf(d - lam) <= td) {
+              ok[r] = false;
+              amb[r] = true;
+            }
+          }
+          // keep the ambiguous samples for the exact path (warp-aggregated append)
+          const unsigned bal = __ballot_sync(0xffffffffu, amb[r]);
+          if (bal) {
+            const int leader = __ffs(bal) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (amb[r]) {
+              const int pos = base + __popc(bal & lanemask_lt);
+              if (pos < kAmbCap) {
+                const int li = threadIdx.x + (g + r) * blockDim.x;
+                const float2 uv = s_UV[li];
+                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
+              } else {
+                // buffer full: evaluate this sample with FP32 decisions instead
+                atomicAdd(a.q_overflow, 1u);
+                ok[r] = (Y2[r] > eps_z) && (up[r] >= 0.f) && (up[r] <= Wm1) && (vp[r] >= 0.f) && (vp[r] <= Hm1);
+                if (ok[r]) {
+                  const int fx0 = min(max(x0[r], 0), P.W - 2), fy0 = min(max(y0[r], 0), P.H - 2);
+                  const float fa = up[r] - (float)fx0, fb = vp[r] - (float)fy0;
+                  float n00, n01, n10, n11;
+                  taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, fx0, fy0, n00, n01, n10, n11);
+                  const float t2 = fmaf(fa, n01 - n00, n00);
+                  const float b2 = fmaf(fa, n11 - n10, n10);
+                  d = fmaf(fb, b2 - t2, t2);
+                  ddu = fmaf(fb, (n11 - n10) - (n01 - n00), n01 - n00);
+                  ddv = b2 - t2;
+                }
               }
             }
           }
-        }
-        if (ok[r]) {
-          // a5: clamp + Huber
-          const float dh = fminf(d, lam);
-          const float adh = fabsf(dh);
-          const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
-          if constexpr (MODE != MODE_BWD) {
-            acc[0] += rho;
-            acc[1] += 1.f;
-          }
-          if constexpr (MODE != MODE_FWD) {
-            // a6: adjoint in camera-j coordinates
-            const float drho = d <= lam ? (fabsf(d) <= delta ? d : copysignf(delta, d)) : 0.f;
-            const float gx = drho * ddu * P.fx * iz[r];
-            const float gy = drho * ddv * P.fy * iz[r];
-            const float gz = -(gx * Y0[r] + gy * Y1[r]) * iz[r];
-            acc[2] += gx;
-            acc[3] += gy;
-            acc[4] += gz;
-            acc[5] += Y1[r] * gz - Y2[r] * gy;
-            acc[6] += Y2[r] * gx - Y0[r] * gz;
-            acc[7] += Y0[r] * gy - Y1[r] * gx;
+          if (ok[r]) {
+            // a5: clamp + Huber
+            const float dh = fminf(d, lam);
+            const float adh = fabsf(dh);
+            const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
+            if constexpr (MODE != MODE_BWD) {
+              acc[0] += rho;
+              acc[1] += 1.f;
+            }
+            if constexpr (MODE != MODE_FWD) {
+              // a6: adjoint in camera-j coordinates
+              const float drho = d <= lam ? (fabsf(d) <= delta ? d : copysignf(delta, d)) : 0.f;
+              const float gx = drho * ddu * P.fx * iz[r];
+              const float gy = drho * ddv * P.fy * iz[r];
+              const float gz = -(gx * Y0[r] + gy * Y1[r]) * iz[r];
+              acc[2] += gx;
+              acc[3] += gy;
+              acc[4] += gz;
+              acc[5] += Y1[r] * gz - Y2[r] * gy;
+              acc[6] += Y2[r] * gx - Y0[r] * gz;
+              acc[7] += Y0[r] * gy - Y1[r] * gx;
+            }
           }
         }
       }
