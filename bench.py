@@ -119,6 +119,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def captured_traffic(gather, block, rpt):
+    """DRAM bytes per edge-kernel launch from the committed ncu capture, or None when the
+    kernel source changed since the capture or this schedule was not captured."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "edge_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(os.path.join(ROOT, d["kernel_source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != d["kernel_source_sha256"]:
+            return None
+    if d.get("workload") != WORKLOAD:
+        return None
+    key = f"{'tex' if gather == 2 else 'ldg'}/{block}/{rpt}"
+    v = d["dram_bytes_per_launch"].get(key)
+    return None if v is None else int(v)
+
+
 # ------------------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------
@@ -316,7 +335,8 @@ def run_ours(args):
     kern_avg = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": captured_traffic(info.gather, info.block_threads, info.records_per_thread),
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
             "kernel": "k_edge<fused,f32,f32>", "kernel_ms": kern_avg,
             "bytes_per_eval": bytes_per_eval}
     st_avg = np.mean(np.array(stages), axis=0)
