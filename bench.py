@@ -3,11 +3,20 @@
 loss + gradient edge kernel, FP64 finalize, FP64 Adam + Exp retraction (one CUDA-graph
 replay).  Prints one JSON line.
 
-Workload (default): a seeded synthetic ring of 32 views at 518x392, each paired with its
-8 nearest views (256 directed pairs), ~20,000 edge pixels per view, FP32 records and maps.
+Workloads (--workload; seeded synthetic scenes, records and maps built on the fly):
+  ring32   (default) 32 views at 518x392 on a ring, each paired with its 8 nearest views
+           (256 directed pairs), ~20,000 edge pixels per view, FP32 records and maps.
+  walk200  200 views at 518x392 on a random walk, 10 neighbours (2,000 pairs), ~30,000 edge
+           pixels per view (6e7 evaluations per step); adds the autograd forward + adjoint
+           timing and the device memory against a stored-Jacobian variant.
+  batch64  64 independent scenes (8..120 views, 256x192 / 518x392 / 518x518, 8 neighbours,
+           2-8 % edge density) batched in one launch per stage; adds the plain per-scene form
+           (64 handles, kernels launched one by one) at equal final pose accuracy.
+  ring500  500 views at 518x518, 12 neighbours (6,000 pairs), BF16 maps and FP16 depth;
+           adds the FP32 form of the same scene and both forms' final pose errors.
 Metric: edge-pixel x pair evaluations per second of the loss + gradient step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 --impl reference times the FP64 CPU oracle (the reference arm for this build) on the host
 cores on the same workload and metric.  For N > 1 (torchrun) every rank runs an
@@ -29,9 +38,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "ring32_518x392_k8_20k_f32"
 METRIC = "edge-pixel*pair evals/s (loss+grad step)"
 UNIT = "evals/s"
+WORKLOADS = {
+    "ring32": "ring32_518x392_k8_20k_f32",
+    "walk200": "walk200_518x392_k10_30k_f32",
+    "batch64": "batch64_uneven_8to120views_k8_f32",
+    "ring500": "ring500_518x518_k12_40k_bf16map_f16depth",
+}
 
 
 def parse():
@@ -40,6 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ring32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -51,9 +66,49 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload():
-    import synth
-    return synth.make_scene(synth.RING32_518x392)
+class Workload:
+    """Seeded synthetic scenes of one benchmark workload, with the stored dtypes."""
+
+    def __init__(self, key):
+        import synth
+        self.key = key
+        self.name = WORKLOADS[key]
+        if key == "ring32":
+            self.scenes = [synth.make_scene(synth.RING32_518x392)]
+        elif key == "walk200":
+            self.scenes = [synth.make_scene(synth.WALK200_518x392)]
+        elif key == "batch64":
+            self.scenes = [synth.make_scene(sp) for sp in synth.batch64_uneven_specs()]
+        elif key == "ring500":
+            self.scenes = [synth.make_scene(synth.RING500_518x518)]
+        else:
+            raise ValueError(key)
+        self.mixed = key == "ring500"  # BF16 maps, FP16 depth records
+
+    @property
+    def T_init(self):
+        return np.concatenate([sc.T_init for sc in self.scenes])
+
+    def parts(self, epo, torch, mixed=None):
+        """Scene parts with device-resident records and maps; the maps are the library's
+        GPU distance fields (rounded to BF16 on the GPU for the mixed form)."""
+        mixed = self.mixed if mixed is None else mixed
+        import synth
+        out = []
+        for sc in self.scenes:
+            maps = [epo.distance_field(torch.from_numpy(e).cuda()) for e in sc.edges]
+            if mixed:
+                maps = [epo.round_bf16(m) for m in maps]
+                rec = torch.from_numpy(synth.records_f16(sc.rec).view(np.int16)).cuda()
+            else:
+                rec = torch.from_numpy(sc.rec).cuda()
+            out.append(dict(W=sc.W, H=sc.H, K=sc.K, rec_off=sc.rec_off, rec=rec, maps=maps, pairs=sc.pairs,
+                            fixed=sc.fixed))
+        return out
+
+    def dtypes(self, epo, mixed=None):
+        mixed = self.mixed if mixed is None else mixed
+        return (epo.EPO_F16, epo.EPO_BF16) if mixed else (epo.EPO_F32, epo.EPO_F32)
 
 
 # ------------------------------------------------------------------------------------------
@@ -141,10 +196,36 @@ def captured_traffic(gather, block, rpt):
 # ------------------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------
-def oracle_scene_for(sc):
+def _bf16_widened(x):
+    """float32 -> nearest bfloat16 (ties to even) -> float32, for finite inputs."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + ((b >> 16) & 1) + 0x7FFF) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def oracle_for_pairs(sc, pair_ids, mixed):
+    """The oracle scene of the given pairs of one synthetic scene: only the views they touch
+    (renumbered), their records and their maps as the GPU stores them (widened)."""
     import oracle
-    maps = [oracle.edt(e).astype(np.float32).astype(np.float64) for e in sc.edges]
-    return oracle.scene_from_synth(sc, maps)
+    import synth
+    pairs = sc.pairs[pair_ids]
+    views = np.unique(pairs)
+    new_id = -np.ones(sc.n_views, dtype=np.int64)
+    new_id[views] = np.arange(len(views))
+    recs, offs = [], [0]
+    for v in views:
+        a, b = sc.rec_off[v], sc.rec_off[v + 1]
+        recs.append(sc.rec[a:b])
+        offs.append(offs[-1] + (b - a))
+    rec = np.concatenate(recs, axis=0)
+    maps = [oracle.edt(sc.edges[v]).astype(np.float32) for v in views]
+    if mixed:
+        rec = synth.records_f16_widened(rec)
+        maps = [_bf16_widened(m) for m in maps]
+    osc = oracle.OracleScene(sc.W[views], sc.H[views], sc.K[views], np.array(offs, dtype=np.int64), rec,
+                             [m.astype(np.float64) for m in maps], new_id[pairs])
+    evals = int(np.diff(sc.rec_off)[pairs[:, 0]].sum())
+    return osc, sc.T_init[views].copy(), sc.fixed[views].copy(), evals
 
 
 def oracle_threads():
@@ -154,70 +235,67 @@ def oracle_threads():
         return os.cpu_count() or 1
 
 
-def time_oracle_steps(sc, osc, n_steps, pair_ids=None):
-    """Run n_steps oracle optimisation steps (loss + gradient + Adam/Exp) on the scene or on a
-    pair subset; returns (seconds, evals processed)."""
-    if pair_ids is not None:
-        osc = _subset(osc, sc, pair_ids)
+def time_oracle_steps(osc, T, fixed, n_steps, step0=0, m=None, v=None):
+    """n_steps oracle optimisation steps (loss + gradient + Adam/Exp); returns (seconds, state)."""
     t0 = time.perf_counter()
-    osc.optimize(sc.T_init, sc.fixed, n_steps, lr_rot=2e-3, lr_trans=2e-2)
-    dt = time.perf_counter() - t0
-    cnt = np.diff(sc.rec_off)
-    pairs = sc.pairs if pair_ids is None else sc.pairs[pair_ids]
-    return dt, int(cnt[pairs[:, 0]].sum()) * n_steps
+    out = osc.optimize(T, fixed, n_steps, lr_rot=2e-3, lr_trans=2e-2, step0=step0, m=m, v=v)
+    return time.perf_counter() - t0, out
 
 
-def _subset(osc, sc, pair_ids):
-    import oracle
-    maps = [osc.map[osc.map_off[v]:osc.map_off[v] + int(sc.W[v]) * int(sc.H[v])].reshape(int(sc.H[v]), int(sc.W[v]))
-            for v in range(sc.n_views)]
-    return oracle.OracleScene(sc.W, sc.H, sc.K, sc.rec_off, sc.rec, maps, sc.pairs[pair_ids])
+def oracle_sample(wl, budget_s, seed=0):
+    """A pair subset of the workload's first scene whose one oracle step takes about
+    budget_s (all pairs when a step takes less): (oracle scene, T, fixed, evals, n_pairs)."""
+    sc = wl.scenes[0]
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(sc.n_pairs)
+    pilot = np.sort(order[: min(8, sc.n_pairs)])
+    osc, T, fx, ev = oracle_for_pairs(sc, pilot, wl.mixed)
+    time_oracle_steps(osc, T, fx, 1)
+    dt, _ = time_oracle_steps(osc, T, fx, 1)
+    rate = ev / max(dt, 1e-6)
+    cnt = np.diff(sc.rec_off)[sc.pairs[order, 0]]
+    n = int(np.searchsorted(np.cumsum(cnt), rate * budget_s)) + 1
+    ids = np.sort(order[: min(max(n, 1), sc.n_pairs)])
+    osc, T, fx, ev = oracle_for_pairs(sc, ids, wl.mixed)
+    return osc, T, fx, ev, len(ids)
 
 
-def cpu_baseline(sc, budget_s=12.0):
-    osc = oracle_scene_for(sc)
-    dt1, ev1 = time_oracle_steps(sc, osc, 1)
+def cpu_baseline(wl, budget_s=12.0):
+    osc, T, fx, ev, n_pairs = oracle_sample(wl, budget_s / 4)
+    dt1, _ = time_oracle_steps(osc, T, fx, 1)
     n = max(1, int(budget_s / max(dt1, 1e-3)))
-    dt, ev = time_oracle_steps(sc, osc, n)
-    return {"value": ev / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"{n} full oracle optimisation steps (FP64, OpenMP over pairs) on the "
-                      f"{WORKLOAD} workload, {ev} evals in {dt:.2f} s"}
+    dt, _ = time_oracle_steps(osc, T, fx, n)
+    return {"value": ev * n / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"{n} oracle optimisation steps (FP64, OpenMP over pairs) on {n_pairs} of the "
+                      f"{wl.scenes[0].n_pairs} pairs of the {'first scene of the ' if len(wl.scenes) > 1 else ''}"
+                      f"{wl.name} workload ({ev} evals per step), {ev * n} evals in {dt:.2f} s"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    sc = make_workload()
-    osc = oracle_scene_for(sc)
-    dt1, _ = time_oracle_steps(sc, osc, 1)
+    wl = Workload(args.workload)
     # each timed step is a bounded sample: a pair subset sized so that the run stays short
     per_step_budget = 150.0 / max(args.steps + args.warmup, 1)
-    frac = min(1.0, per_step_budget / max(dt1, 1e-6))
-    rng = np.random.default_rng(0)
-    n_pairs = max(1, int(round(frac * sc.n_pairs)))
-    ids = None if n_pairs >= sc.n_pairs else np.sort(rng.choice(sc.n_pairs, n_pairs, replace=False))
-    sub = osc if ids is None else _subset(osc, sc, ids)
-    pairs = sc.pairs if ids is None else sc.pairs[ids]
-    evals = int(np.diff(sc.rec_off)[pairs[:, 0]].sum())
-    T = sc.T_init.copy()
+    osc, T, fx, evals, n_pairs = oracle_sample(wl, per_step_budget)
     m = v = None
     step = 0
     for _ in range(args.warmup):
-        T, m, v, _ = sub.optimize(T, sc.fixed, 1, lr_rot=2e-3, lr_trans=2e-2, step0=step, m=m, v=v)
+        _, (T, m, v, _) = time_oracle_steps(osc, T, fx, 1, step, m, v)
         step += 1
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        T, m, v, _ = sub.optimize(T, sc.fixed, 1, lr_rot=2e-3, lr_trans=2e-2, step0=step, m=m, v=v)
+        _, (T, m, v, _) = time_oracle_steps(osc, T, fx, 1, step, m, v)
         step += 1
     dt = time.perf_counter() - t0
     val = evals * args.steps / dt
-    sample = (f"each step = oracle loss+grad+Adam/Exp on {len(pairs)} of {sc.n_pairs} pairs "
-              f"({evals} evals) of the {WORKLOAD} workload")
+    sample = (f"each step = oracle loss+grad+Adam/Exp on {n_pairs} of {wl.scenes[0].n_pairs} pairs "
+              f"({evals} evals) of the {wl.name} workload")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "data": "synthetic", "config": {"workload": wl.name, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -228,6 +306,35 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
+def pose_errors(T, scenes):
+    """Mean rotation error (degrees) and mean camera-centre error (fraction of the scene
+    scale) of stacked poses T against the scenes' ground truth."""
+    rot, tr, off = [], [], 0
+    for sc in scenes:
+        for v in range(sc.n_views):
+            A = T[off + v].reshape(3, 4)
+            G = sc.T_gt[v].reshape(3, 4)
+            c = (np.trace(A[:, :3] @ G[:, :3].T) - 1) / 2
+            rot.append(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+            ca, cg = -A[:, :3].T @ A[:, 3], -G[:, :3].T @ G[:, 3]
+            tr.append(np.linalg.norm(ca - cg) / sc.scale)
+        off += sc.n_views
+    return float(np.mean(rot)), float(np.mean(tr))
+
+
+def time_steps(h, n, flush_l2, stream, torch):
+    """n flushed, event-timed graph steps of handle h; returns per-step ms."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush_l2(k)
+        ev[k][0].record(stream)
+        h.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    h.check()
+    return [x.elapsed_time(y) for x, y in ev]
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -237,26 +344,27 @@ def run_ours(args):
         dist.init_process_group("nccl")
     import paper_2607_00579_gb300 as epo
 
-    sc = make_workload()
+    wl = Workload(args.workload)
     stream = torch.cuda.current_stream()
+    T_init = wl.T_init
     # distance transform fields built on the GPU by the library (construction step)
-    maps_dev = [epo.distance_field(torch.from_numpy(e).cuda()) for e in sc.edges]
-    rec_dev = torch.from_numpy(sc.rec).cuda()
-    part = dict(W=sc.W, H=sc.H, K=sc.K, rec_off=sc.rec_off, rec=rec_dev, maps=maps_dev, pairs=sc.pairs,
-                fixed=sc.fixed)
-    opts = epo.default_options(autotune=2, lr_rot=2e-3, lr_trans=2e-2)
-    s = epo.Scene([part], options=opts, on_device=True)
-    s.set_poses(sc.T_init)
+    parts = wl.parts(epo, torch)
+    rd, md = wl.dtypes(epo)
+    lr = dict(lr_rot=2e-3, lr_trans=2e-2)
+
+    def scene(options, prts=parts, dt=(rd, md)):
+        return epo.Scene(prts, record_dtype=dt[0], map_dtype=dt[1], options=options, on_device=True)
+
+    s = scene(epo.default_options(autotune=2, **lr))
+    s.set_poses(T_init)
     s.autotune()
     info = s.info()
     evals = info.evals_per_step
-    k_pairs = sc.n_pairs / sc.n_views
     # a second handle on the same workload and schedule, with CUDA events captured around
     # each stage inside its graph: kernel and stage times come from it, so that the events
     # do not perturb the headline step time
-    topts = epo.default_options(timing=1, lr_rot=2e-3, lr_trans=2e-2, gather=info.gather,
-                                block_threads=info.block_threads, records_per_thread=info.records_per_thread)
-    st_ = epo.Scene([part], options=topts, on_device=True)
+    sched = dict(gather=info.gather, block_threads=info.block_threads, records_per_thread=info.records_per_thread)
+    st_ = scene(epo.default_options(timing=1, **lr, **sched))
     # L2 flush between timed steps: write a 512 MB buffer (4x the L2), then read half of it
     # back, so that the step starts with an L2 full of clean lines unrelated to its inputs
     # (a write alone would leave 126 MB of dirty lines whose write-backs the step would pay)
@@ -268,14 +376,13 @@ def run_ours(args):
         flush_sink.copy_(flush[: flush.numel() // 2].sum().reshape(1))
 
     for h in (s, st_):
-        h.set_poses(sc.T_init)
+        h.set_poses(T_init)
         for _ in range(args.warmup):
             h.step_async(1)
         torch.cuda.synchronize()
-        h.set_poses(sc.T_init)
+        h.set_poses(T_init)
         h.set_state(0)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -284,15 +391,8 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush_l2(k)
-        ev[k][0].record(stream)
-        s.step_async(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = time_steps(s, args.steps, flush_l2, stream, torch)
     t_wall = time.perf_counter() - t_wall0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    s.check()
     # kernel and stage times over the same number of flushed steps on the timed handle
     kern_ms, stages = [], []
     for k in range(args.steps):
@@ -311,7 +411,7 @@ def run_ours(args):
     value = world * evals * args.steps / (tot_ms * 1e-3)
 
     # end to end through the public API with host buffers: pinned poses in, step, poses + loss out
-    T_host = torch.from_numpy(sc.T_init.copy()).pin_memory()
+    T_host = torch.from_numpy(T_init.copy()).pin_memory()
     T_out = torch.empty_like(T_host).pin_memory()
     loss_out = torch.empty(info.n_scenes, dtype=torch.float64).pin_memory()
     e2e_steps = max(10, args.steps // 2)
@@ -328,24 +428,29 @@ def run_ours(args):
            "h2d_bytes_per_step": int(T_host.numel() * 8),
            "d2h_bytes_per_step": int(T_out.numel() * 8 + loss_out.numel() * 8)}
 
-    # roofline of the dominant kernel (fused loss + gradient edge kernel)
+    # roofline of the dominant kernel (fused loss + gradient edge kernel): the four taps of
+    # every evaluation, plus every record once per step (shared by its view's pairs)
     peak, peak_src = measured_peaks()
-    bytes_per_eval = 4 * 4 + 16 / k_pairs  # 2x2 f32 taps + one 16-byte record shared by k pairs
-    alg_bytes = evals * bytes_per_eval
+    s_map = 2 if wl.mixed else 4
+    s_rec = 8 if wl.mixed else 16
+    alg_bytes = evals * 4 * s_map + info.n_records * s_rec
     kern_avg = float(np.mean(kern_ms))
     achieved = alg_bytes / (kern_avg * 1e-3) / 1e9
+    traffic = captured_traffic(info.gather, info.block_threads, info.records_per_thread) \
+        if wl.key == "ring32" else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": captured_traffic(info.gather, info.block_threads, info.records_per_thread),
-            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-            "kernel": "k_edge<fused,f32,f32>", "kernel_ms": kern_avg,
-            "bytes_per_eval": bytes_per_eval}
+            "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "kernel": "k_edge (fused loss + gradient)", "kernel_ms": kern_avg,
+            "bytes_per_eval": alg_bytes / evals, "algorithmic_bytes_per_launch": alg_bytes}
     st_avg = np.mean(np.array(stages), axis=0)
     queued, overflow = epo._binding.epo_fixup_stats(st_.handle)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "views": sc.n_views, "pairs": sc.n_pairs,
-                       "evals_per_step": evals, "l2": "flushed between timed steps (512 MB write, then 256 MB read back)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f16 gathers, f32" if wl.mixed else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "scenes": info.n_scenes, "views": info.n_views,
+                       "pairs": info.n_pairs, "records": info.n_records, "evals_per_step": evals,
+                       "l2": "flushed between timed steps (512 MB write, then 256 MB read back)",
                        "schedule": {"gather": info.gather, "block": info.block_threads,
                                     "records_per_thread": info.records_per_thread,
                                     "grid": info.grid_blocks},
@@ -355,14 +460,139 @@ def run_ours(args):
                           "poses": float(st_avg[2])},
             "exact_fixup_samples": queued, "exact_fixup_overflow": overflow,
             "wall_ms_per_step": 1e3 * t_wall / args.steps}
+    del st_
+    if wl.key == "walk200":
+        line["autograd"] = autograd_leg(epo, torch, s, T_init, evals, args, flush_l2, stream)
+    elif wl.key == "batch64":
+        leg = plain_per_scene_leg(epo, torch, wl, s, parts, (rd, md), lr, evals, args, flush_l2, stream)
+        leg["speedup_of_batched_graph_step"] = leg["ms_per_step"] / (tot_ms / args.steps)
+        line["plain_per_scene"] = leg
+    elif wl.key == "ring500":
+        line["fp32_form"] = fp32_form_leg(epo, torch, wl, s, scene, lr, evals, args, flush_l2, stream)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc)
+        line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+ACC_STEPS = 100  # optimisation steps behind the final-accuracy comparisons
+
+
+def autograd_leg(epo, torch, s, T_init, evals, args, flush_l2, stream):
+    """Forward + adjoint through the autograd function at the current poses (two passes over
+    the samples: the adjoint recomputes every projection instead of storing per-sample
+    Jacobians), and the device memory this takes against a stored-Jacobian variant."""
+    s.set_poses(T_init)
+    xi = torch.zeros((s.n_views, 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    for _ in range(3):
+        epo.EdgeLoss.apply(xi, s).sum().backward()
+    xi.grad = None
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    n = max(5, min(args.steps, 50))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush_l2(k)
+        ev[k][0].record(stream)
+        epo.EdgeLoss.apply(xi, s).sum().backward()
+        ev[k][1].record(stream)
+        xi.grad = None
+    torch.cuda.synchronize()
+    ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    info = s.info()
+    return {"value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_forward_backward": ms, "iterations": n,
+            "torch_peak_bytes_above_inputs": int(torch.cuda.max_memory_allocated() - base),
+            "library_device_bytes": int(info.device_bytes),
+            "inputs_bytes": int(info.record_bytes + info.map_bytes),
+            "stored_jacobian_bytes": int(evals * 14 * 4),
+            "note": "stored-Jacobian variant: per evaluation d(rho)/d(xi_i), d(rho)/d(xi_j) (2 x 6 FP32), "
+                    "rho and the validity flag, on top of the same inputs"}
+
+
+def plain_per_scene_leg(epo, torch, wl, s, parts, dtypes, lr, evals, args, flush_l2, stream):
+    """The per-scene plain form: one handle per scene with the default schedule, the same
+    kernels launched one by one from the host each step (host-side synchronisation per
+    scene), against the batched graph step; then both forms run ACC_STEPS steps from the
+    initial poses and their final pose errors are compared."""
+    hs = [epo.Scene([p], record_dtype=dtypes[0], map_dtype=dtypes[1],
+                    options=epo.default_options(**lr), on_device=True) for p in parts]
+    for h, sc in zip(hs, wl.scenes):
+        h.set_poses(sc.T_init)
+        h.step_plain(1)
+    n = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for k in range(n):
+        flush_l2(k)
+        e0.record(stream)
+        for h in hs:
+            h.step_plain(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    plain_ms = tot / n
+    # equal final accuracy: both forms from the initial poses, ACC_STEPS steps
+    s.set_poses(wl.T_init)
+    s.set_state(0)
+    s.step(ACC_STEPS)
+    Tb = s.get_poses()
+    Tp = []
+    for h, sc in zip(hs, wl.scenes):
+        h.set_poses(sc.T_init)
+        h.set_state(0)
+        h.step_plain(ACC_STEPS)
+        Tp.append(h.get_poses())
+    Tp = np.concatenate(Tp)
+    del hs
+    r0, t0 = pose_errors(wl.T_init, wl.scenes)
+    rb, tb = pose_errors(Tb, wl.scenes)
+    rp, tp = pose_errors(Tp, wl.scenes)
+    return {"value": evals / (plain_ms * 1e-3), "unit": UNIT, "ms_per_step": plain_ms, "steps": n,
+            "schedule": "library default (block 256, 2 records per thread, plain loads), no autotuning",
+            "speedup_of_batched_graph_step": None,
+            "final_accuracy": {"steps": ACC_STEPS, "initial_rot_deg": r0, "initial_trans_frac": t0,
+                               "batched_graph_rot_deg": rb, "batched_graph_trans_frac": tb,
+                               "plain_per_scene_rot_deg": rp, "plain_per_scene_trans_frac": tp,
+                               "max_abs_pose_difference": float(np.abs(Tb - Tp).max())}}
+
+
+def fp32_form_leg(epo, torch, wl, s, scene, lr, evals, args, flush_l2, stream):
+    """The same scene with FP32 maps and records (autotuned the same way): its step
+    throughput, and both forms' final pose errors after ACC_STEPS steps."""
+    parts32 = wl.parts(epo, torch, mixed=False)
+    s32 = scene(epo.default_options(autotune=2, **lr), prts=parts32, dt=wl.dtypes(epo, mixed=False))
+    s32.set_poses(wl.T_init)
+    s32.autotune()
+    for _ in range(3):
+        s32.step_async(1)
+    s32.set_poses(wl.T_init)
+    s32.set_state(0)
+    ms32 = float(np.mean(time_steps(s32, max(5, min(args.steps, 50)), flush_l2, stream, torch)))
+    res = {}
+    for name, h in (("bf16_f16", s), ("fp32", s32)):
+        h.set_poses(wl.T_init)
+        h.set_state(0)
+        h.step(ACC_STEPS)
+        res[name] = h.get_poses()
+    r0, t0 = pose_errors(wl.T_init, wl.scenes)
+    ra, ta = pose_errors(res["bf16_f16"], wl.scenes)
+    rf, tf = pose_errors(res["fp32"], wl.scenes)
+    sc = wl.scenes[0]
+    Ta, Tf = res["bf16_f16"].reshape(-1, 3, 4), res["fp32"].reshape(-1, 3, 4)
+    dR = [np.degrees(np.arccos(np.clip((np.trace(a[:, :3] @ f[:, :3].T) - 1) / 2, -1, 1))) for a, f in zip(Ta, Tf)]
+    dC = [np.linalg.norm(-a[:, :3].T @ a[:, 3] + f[:, :3].T @ f[:, 3]) / sc.scale for a, f in zip(Ta, Tf)]
+    return {"value": evals / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
+            "final_accuracy": {"steps": ACC_STEPS, "initial_rot_deg": r0, "initial_trans_frac": t0,
+                               "bf16_f16_rot_deg": ra, "bf16_f16_trans_frac": ta,
+                               "fp32_rot_deg": rf, "fp32_trans_frac": tf,
+                               "max_rot_deg_between_forms": float(np.max(dR)),
+                               "max_trans_frac_between_forms": float(np.max(dC))}}
 
 
 def main():

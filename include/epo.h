@@ -248,6 +248,24 @@ epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, fl
 /* Round n floats to bfloat16 (round to nearest even), device buffers. */
 epo_status epo_round_bf16(const float* src_dev, uint16_t* dst_dev, int64_t n, void* cuda_stream);
 
+/* Gather-throughput probe for the roofline of the sampling step (Eq. 8's
+ * bilinear sample; the paper names projection and sampling as the dominant
+ * cost, Section 5 / Appendix A): 2x2 footprints per second that this GPU
+ * serves from n_maps maps of W x H (map_dtype EPO_F32 or EPO_BF16, rows
+ * padded to 128 bytes as in a scene), fetched with the edge kernel's form
+ * (gather = EPO_GATHER_LDG: four read-only loads; EPO_GATHER_TEX: one
+ * texture gather).  pattern 0: independent uniform positions per thread;
+ * 1: the 32 lanes of a warp along a 32-pixel segment at a random place (the
+ * locality of consecutive edge pixels; needs W >= 48, H >= 16).  About
+ * `samples` footprints per launch; the median of `repeats` timed launches
+ * (after two that fill L2) is written to *samples_per_s.  The buffers are
+ * allocated and freed inside the call; synchronises the stream.  Invalid
+ * sizes or modes: EPO_ERR_INVALID_ARG; a failed CUDA call: EPO_ERR_CUDA
+ * (everything allocated is freed). */
+epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dtype, int32_t gather,
+                            int32_t pattern, int64_t samples, int32_t repeats, double* samples_per_s,
+                            void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Loss and gradient without any device allocation.
  *

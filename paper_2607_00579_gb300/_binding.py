@@ -38,7 +38,7 @@ EXPORTED = [
     "epo_loss_and_grad_dev", "epo_pair_stats", "epo_forward_dev", "epo_backward_dev", "epo_step",
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
-    "epo_loss_and_grad_noalloc",
+    "epo_loss_and_grad_noalloc", "epo_gather_probe",
 ]
 
 
@@ -271,3 +271,13 @@ def epo_distance_field(edges_dev, W: int, H: int, map_dev, stream: int = 0):
 
 def epo_round_bf16(src_dev, dst_dev, n: int, stream: int = 0):
     check(load().epo_round_bf16(_ptr(src_dev), _ptr(dst_dev), ctypes.c_int64(n), ctypes.c_void_p(stream)))
+
+
+def epo_gather_probe(n_maps: int, W: int, H: int, map_dtype: int, gather: int, pattern: int, samples: int,
+                     repeats: int = 5, stream: int = 0) -> float:
+    out = ctypes.c_double(0.0)
+    check(load().epo_gather_probe(ctypes.c_int32(n_maps), ctypes.c_int32(W), ctypes.c_int32(H),
+                                  ctypes.c_int32(map_dtype), ctypes.c_int32(gather), ctypes.c_int32(pattern),
+                                  ctypes.c_int64(samples), ctypes.c_int32(repeats), ctypes.byref(out),
+                                  ctypes.c_void_p(stream)))
+    return out.value

@@ -76,7 +76,13 @@ struct epo_scene {
   ViewDev* d_views = nullptr;
   TileDev* d_tiles = nullptr;
   int32_t n_tiles = 0;
-  int tiles_for = -1;  // tile size the table was built for
+  int tiles_for = -1;  // tile size the current table was built for
+  struct TileTable {
+    int tile;
+    TileDev* p;
+    int32_t n;
+  };
+  std::vector<TileTable> tile_tables;  // every table built so far, kept for cheap switches
   int32_t *d_src_pair_off = nullptr, *d_src_pair_ids = nullptr, *d_pair_src = nullptr,
           *d_pair_dst = nullptr, *d_pair_scene = nullptr, *d_scene_pair_off = nullptr,
           *d_scene_active = nullptr, *d_pose_pair_off = nullptr, *d_pose_pair_ref = nullptr;
@@ -195,6 +201,14 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
 
 epo_status build_tiles(epo_scene* S, int tile) {
   if (S->tiles_for == tile) return EPO_OK;
+  S->graph_dirty = true;
+  for (const auto& tt : S->tile_tables)
+    if (tt.tile == tile) {
+      S->d_tiles = tt.p;
+      S->n_tiles = tt.n;
+      S->tiles_for = tile;
+      return EPO_OK;
+    }
   std::vector<TileDev> t;
   for (int v = 0; v < S->n_views; ++v) {
     const ViewDev& vd = S->views[v];
@@ -207,20 +221,13 @@ epo_status build_tiles(epo_scene* S, int tile) {
       t.push_back(td);
     }
   }
-  if (S->d_tiles) {
-    cudaFree(S->d_tiles);
-    for (auto& b : S->bufs)
-      if (b.p == S->d_tiles) {
-        S->device_bytes -= (int64_t)b.n;
-        b.p = nullptr;
-      }
-    S->d_tiles = nullptr;
-  }
-  ALLOC(S->d_tiles, t.size());
-  if (!t.empty()) CK(cudaMemcpy(S->d_tiles, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+  TileDev* d = nullptr;
+  ALLOC(d, t.size());
+  if (!t.empty()) CK(cudaMemcpy(d, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
+  S->tile_tables.push_back({tile, d, (int32_t)t.size()});
+  S->d_tiles = d;
   S->n_tiles = (int32_t)t.size();
   S->tiles_for = tile;
-  S->graph_dirty = true;
   return EPO_OK;
 }
 
@@ -965,12 +972,29 @@ epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
   return EPO_OK;
 }
 
+// Times every schedule of the edge kernel on this scene and keeps the fastest. Launches of
+// different candidates are interleaved (one launch of each per pass), so that clock or
+// thermal drift during tuning affects all of them alike, and each candidate is judged by
+// the median of its launches. A first pass over all candidates (3 timed launches each)
+// keeps the 4 best; 12 further passes decide between those.
 epo_status epo_autotune(epo_scene_t S) {
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   S->tuned = true;  // also guards against recursion through maybe_autotune
-  const int gathers[2] = {GATHER_LDG, GATHER_TEX};
-  const int rpts[3] = {1, 2, 4};
-  const int blocks[3] = {128, 256, 512};
+  struct Cand {
+    int g, r, b;
+    std::vector<float> ms;
+    float med;
+  };
+  std::vector<Cand> cands;
+  for (int g : {GATHER_LDG, GATHER_TEX})
+    for (int r : {1, 2, 4})
+      for (int b : {128, 256, 512}) {
+        if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
+        if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
+        if (!schedule_fits(S, r, b)) continue;
+        cands.push_back({g, r, b, {}, 0.f});
+      }
+  if (cands.empty()) return fail(S, EPO_ERR_INVALID_ARG, "no edge-kernel schedule fits this scene");
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -986,47 +1010,63 @@ epo_status epo_autotune(epo_scene_t S) {
     flush_bytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20);
     CK(cudaMalloc(&flush, flush_bytes + 16));
   }
-  float best = 1e30f;
-  int bg = S->gather, br = S->rpt, bb = S->block;
-  for (int g : gathers)
-    for (int r : rpts)
-      for (int b : blocks) {
-        if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
-        if (!schedule_fits(S, r, b)) continue;
-        if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
-        float tot = 0.f;
-        for (int it = 0; it < 4; ++it) {
-          if (flush) {
-            CK(cudaMemsetAsync(flush, it + 1, flush_bytes, S->stream));
-            CK(launch_l2_read(flush, (int64_t)flush_bytes / 2, (unsigned*)((char*)flush + flush_bytes),
-                              S->sm_count, S->stream));
-          }
-          CK(launch_pair_setup(a, MODE_FUSED, S->stream));
-          CK(cudaEventRecord(e0, S->stream));
-          epo_status st = run_edge(S, MODE_FUSED, g, r, b, S->stream);
-          if (st != EPO_OK) return st;
-          CK(cudaEventRecord(e1, S->stream));
-          CK(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          CK(cudaEventElapsedTime(&ms, e0, e1));
-          if (it > 0) tot += ms;  // first launch is a warm-up
-        }
-        if (tot < best) {
-          best = tot;
-          bg = g; br = r; bb = b;
-        }
-      }
+  int fill = 0;
+  // one launch of candidate c; its time is appended when `timed`
+  auto launch = [&](Cand& c, bool timed) -> epo_status {
+    epo_status st = build_tiles(S, c.b * c.r);  // outside the timed interval
+    if (st != EPO_OK) return st;
+    if (flush) {
+      CK(cudaMemsetAsync(flush, ++fill & 0xff, flush_bytes, S->stream));
+      CK(launch_l2_read(flush, (int64_t)flush_bytes / 2, (unsigned*)((char*)flush + flush_bytes), S->sm_count,
+                        S->stream));
+    }
+    CK(launch_pair_setup(a, MODE_FUSED, S->stream));
+    CK(cudaEventRecord(e0, S->stream));
+    st = run_edge(S, MODE_FUSED, c.g, c.r, c.b, S->stream);
+    if (st != EPO_OK) return st;
+    CK(cudaEventRecord(e1, S->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (timed) c.ms.push_back(ms);
+    return EPO_OK;
+  };
+  auto median = [](std::vector<float> v) {
+    std::sort(v.begin(), v.end());
+    const size_t n = v.size();
+    return n % 2 ? v[n / 2] : 0.5f * (v[n / 2 - 1] + v[n / 2]);
+  };
+  epo_status st = EPO_OK;
+  for (auto& c : cands)
+    if ((st = launch(c, false)) != EPO_OK) break;  // warm-up: module load, first touch
+  for (int pass = 0; pass < 3 && st == EPO_OK; ++pass)
+    for (auto& c : cands)
+      if ((st = launch(c, true)) != EPO_OK) break;
+  if (st == EPO_OK) {
+    for (auto& c : cands) c.med = median(c.ms);
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.med < y.med; });
+    if (cands.size() > 4) cands.resize(4);
+    for (int pass = 0; pass < 12 && st == EPO_OK; ++pass)
+      for (auto& c : cands)
+        if ((st = launch(c, true)) != EPO_OK) break;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (flush) {
-    CK(cudaStreamSynchronize(S->stream));
-    CK(cudaFree(flush));
+    cudaStreamSynchronize(S->stream);
+    cudaFree(flush);
   }
-  S->gather = bg;
-  S->rpt = br;
-  S->block = bb;
+  if (st != EPO_OK) return st;
+  const Cand* best = &cands[0];
+  for (auto& c : cands) {
+    c.med = median(c.ms);
+    if (c.med < best->med) best = &c;
+  }
+  S->gather = best->g;
+  S->rpt = best->r;
+  S->block = best->b;
   S->graph_dirty = true;
-  return build_tiles(S, bb * br);
+  return build_tiles(S, S->block * S->rpt);
 }
 
 epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, float* map_dev,

@@ -1,0 +1,213 @@
+// Gather-throughput probe: how many 2x2 map footprints per second this GPU serves from an
+// L2-resident set of maps, with the same two fetch forms as the edge kernel (four read-only
+// loads, or one texture gather).  The rate bounds the edge kernel's sampling step (a4) from
+// above and gives the second term of its roofline (tap bytes / gather bandwidth).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/epo.h"
+#include "epo_internal.cuh"
+
+using epo::GATHER_LDG;
+using epo::GATHER_TEX;
+
+namespace {
+
+// lowbias32 (C. Wellons' published 32-bit integer hash): uniform bits for sample positions.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+__global__ void k_probe_fill(float* map, int64_t n, int pitch) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i % pitch, y = i / pitch;
+    map[i] = 0.25f * (float)((x * 7 + y * 13) % 97);
+  }
+}
+
+__global__ void k_probe_to_bf16(const float* src, unsigned short* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (unsigned short)(__float_as_uint(src[i]) >> 16);  // exact: the fill values have short mantissas
+}
+
+// PATTERN 0: every lane samples an independent uniform position of a random map.
+// PATTERN 1: the lanes of a warp sample 32 points along a short segment (1.1 px apart in u,
+// 0.37 px in v) at a random place of a random map, the way consecutive edge pixels of a
+// view land in a paired view.
+template <int MAP, int GATHER, int PATTERN>
+__global__ void __launch_bounds__(256) k_gather_probe(const void* maps, const unsigned long long* tex, int W, int H,
+                                                      int pitch, int64_t map_stride, int n_maps, int iters,
+                                                      float* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t warp = tid >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const float span_u = PATTERN ? (float)W - 40.0f : (float)W - 1.001f;
+  const float span_v = PATTERN ? (float)H - 14.0f : (float)H - 1.001f;
+  float acc = 0.0f;
+  for (int i = 0; i < iters; ++i) {
+    const uint32_t h = hash32(warp * 0x9E3779B9u + (uint32_t)i);
+    const int m = (int)(h % (uint32_t)n_maps);
+    float u, v;
+    if (PATTERN == 0) {
+      const uint32_t q = hash32(h ^ (lane * 0x85EBCA6Bu + 1u));
+      u = (float)(q & 0xffffu) * (span_u / 65535.0f);
+      v = (float)(q >> 16) * (span_v / 65535.0f);
+    } else {
+      const uint32_t q = hash32(h + 0x27D4EB2Fu);
+      u = (float)(q & 0xffffu) * (span_u / 65535.0f) + 1.1f * (float)lane;
+      v = (float)(q >> 16) * (span_v / 65535.0f) + 0.37f * (float)lane;
+    }
+    const int x0 = min((int)u, W - 2), y0 = min((int)v, H - 2);
+    float m00, m01, m10, m11;
+    if (GATHER == GATHER_TEX) {
+      const float fx = (float)x0 + 1.0f, fy = (float)y0 + 1.0f;
+      if (MAP == 0) {
+        const float4 g = tex2Dgather<float4>((cudaTextureObject_t)tex[m], fx, fy, 0);
+        m00 = g.w; m01 = g.z; m10 = g.x; m11 = g.y;
+      } else {
+        const ushort4 g = tex2Dgather<ushort4>((cudaTextureObject_t)tex[m], fx, fy, 0);
+        m00 = __uint_as_float((unsigned)g.w << 16); m01 = __uint_as_float((unsigned)g.z << 16);
+        m10 = __uint_as_float((unsigned)g.x << 16); m11 = __uint_as_float((unsigned)g.y << 16);
+      }
+    } else if (MAP == 0) {
+      const float* p = reinterpret_cast<const float*>(maps) + m * map_stride + (int64_t)y0 * pitch + x0;
+      m00 = __ldg(p); m01 = __ldg(p + 1); m10 = __ldg(p + pitch); m11 = __ldg(p + pitch + 1);
+    } else {
+      const unsigned short* p =
+          reinterpret_cast<const unsigned short*>(maps) + m * map_stride + (int64_t)y0 * pitch + x0;
+      m00 = __uint_as_float((unsigned)__ldg(p) << 16); m01 = __uint_as_float((unsigned)__ldg(p + 1) << 16);
+      m10 = __uint_as_float((unsigned)__ldg(p + pitch) << 16);
+      m11 = __uint_as_float((unsigned)__ldg(p + pitch + 1) << 16);
+    }
+    acc += (m00 + m01) + (m10 + m11);
+  }
+  if (acc == -1.0f) sink[0] = acc;  // never true (the maps are >= 0): keeps the loads live
+}
+
+template <int MAP, int GATHER>
+const void* probe_ptr(int pattern) {
+  return pattern ? (const void*)k_gather_probe<MAP, GATHER, 1> : (const void*)k_gather_probe<MAP, GATHER, 0>;
+}
+
+const void* probe_kernel(int map, int gather, int pattern) {
+  if (gather == GATHER_TEX) return map ? probe_ptr<1, GATHER_TEX>(pattern) : probe_ptr<0, GATHER_TEX>(pattern);
+  return map ? probe_ptr<1, GATHER_LDG>(pattern) : probe_ptr<0, GATHER_LDG>(pattern);
+}
+
+}  // namespace
+
+extern "C" epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dtype, int32_t gather,
+                                       int32_t pattern, int64_t samples, int32_t repeats, double* samples_per_s,
+                                       void* cuda_stream) {
+  if (!samples_per_s || n_maps < 1 || W < 2 || H < 2 || W > 65535 || H > 65535 || samples < 1 || repeats < 1 ||
+      (map_dtype != EPO_F32 && map_dtype != EPO_BF16) || (gather != EPO_GATHER_LDG && gather != EPO_GATHER_TEX) ||
+      (pattern != 0 && pattern != 1) || (pattern == 1 && (W < 48 || H < 16)))
+    return EPO_ERR_INVALID_ARG;
+  const int map = map_dtype == EPO_BF16 ? 1 : 0;
+  const size_t esz = map ? 2 : 4;
+  const int pitch = (int)(((int64_t)W + 127 / (int64_t)esz) / (128 / (int64_t)esz) * (128 / (int64_t)esz));
+  const int64_t stride = (int64_t)pitch * H;
+  const int64_t n = stride * n_maps;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float* f32 = nullptr;
+  void* maps = nullptr;
+  float* sink = nullptr;
+  unsigned long long* d_tex = nullptr;
+  std::vector<cudaArray_t> arrays(n_maps, nullptr);
+  std::vector<unsigned long long> tex(n_maps, 0ull);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  epo_status rc = EPO_OK;
+  std::vector<float> ms;
+  int dev = 0, sms = 0, per_sm = 0;
+  const void* kern = probe_kernel(map, gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG, pattern);
+#define PK(call)                                                                  \
+  do {                                                                            \
+    if ((call) != cudaSuccess) {                                                  \
+      rc = EPO_ERR_CUDA;                                                          \
+      goto done;                                                                  \
+    }                                                                             \
+  } while (0)
+  PK(cudaMalloc(&f32, (size_t)n * 4));
+  PK(cudaMalloc(&sink, 16));
+  k_probe_fill<<<1024, 256, 0, st>>>(f32, n, pitch);
+  PK(cudaGetLastError());
+  if (map) {
+    PK(cudaMalloc(&maps, (size_t)n * 2));
+    k_probe_to_bf16<<<1024, 256, 0, st>>>(f32, (unsigned short*)maps, n);
+    PK(cudaGetLastError());
+  } else {
+    maps = f32;
+  }
+  if (gather == EPO_GATHER_TEX) {
+    cudaChannelFormatDesc cfd = map ? cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned)
+                                    : cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    for (int m = 0; m < n_maps; ++m) {
+      PK(cudaMallocArray(&arrays[m], &cfd, W, H, cudaArrayTextureGather));
+      PK(cudaMemcpy2DToArrayAsync(arrays[m], 0, 0, (const uint8_t*)maps + m * stride * esz, (size_t)pitch * esz,
+                                  (size_t)W * esz, H, cudaMemcpyDeviceToDevice, st));
+      cudaResourceDesc rd = {};
+      rd.resType = cudaResourceTypeArray;
+      rd.res.array.array = arrays[m];
+      cudaTextureDesc td = {};
+      td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+      td.filterMode = cudaFilterModePoint;
+      td.readMode = cudaReadModeElementType;
+      td.normalizedCoords = 0;
+      cudaTextureObject_t t = 0;
+      PK(cudaCreateTextureObject(&t, &rd, &td, nullptr));
+      tex[m] = (unsigned long long)t;
+    }
+    PK(cudaMalloc(&d_tex, (size_t)n_maps * 8));
+    PK(cudaMemcpyAsync(d_tex, tex.data(), (size_t)n_maps * 8, cudaMemcpyHostToDevice, st));
+  }
+  PK(cudaGetDevice(&dev));
+  PK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+  PK(cudaEventCreate(&e0));
+  PK(cudaEventCreate(&e1));
+  {
+    const int grid = sms * std::max(per_sm, 1);
+    const int64_t threads = (int64_t)grid * 256;
+    const int iters = (int)std::max<int64_t>(1, std::min<int64_t>((samples + threads - 1) / threads, 1 << 20));
+    const void* mp = maps;
+    const unsigned long long* tp = d_tex;
+    int w = W, h = H, pt = pitch, nm = n_maps, it = iters;
+    int64_t sd = stride;
+    void* args[] = {(void*)&mp, (void*)&tp, (void*)&w, (void*)&h, (void*)&pt, (void*)&sd, (void*)&nm, (void*)&it,
+                    (void*)&sink};
+    for (int r = 0; r < repeats + 2; ++r) {
+      PK(cudaEventRecord(e0, st));
+      PK(cudaLaunchKernel(kern, dim3(grid), dim3(256), args, 0, st));
+      PK(cudaEventRecord(e1, st));
+      PK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      PK(cudaEventElapsedTime(&t, e0, e1));
+      if (r >= 2) ms.push_back(t);  // two warm-up launches fill L2
+    }
+    std::sort(ms.begin(), ms.end());
+    *samples_per_s = (double)threads * iters / (ms[ms.size() / 2] * 1e-3);
+  }
+done:
+#undef PK
+  if (st) cudaStreamSynchronize(st);
+  else cudaDeviceSynchronize();
+  for (auto t : tex)
+    if (t) cudaDestroyTextureObject((cudaTextureObject_t)t);
+  for (auto a : arrays)
+    if (a) cudaFreeArray(a);
+  if (d_tex) cudaFree(d_tex);
+  if (map && maps) cudaFree(maps);
+  if (f32) cudaFree(f32);
+  if (sink) cudaFree(sink);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}

@@ -213,11 +213,11 @@ def _smooth_noise(rng: np.random.Generator, W: int, H: int, sigma: float) -> np.
 
     def interp_matrix(coords, n):
         M = np.zeros((len(coords), n))
-        for i, c in enumerate(coords):
-            b = int(np.floor(c))
-            for k in range(b - 1, b + 3):
-                kk = min(max(k, 0), n - 1)
-                M[i, kk] += keys(c - k)
+        rows = np.arange(len(coords))
+        b = np.floor(coords).astype(np.int64)
+        for o in range(-1, 3):  # the four taps, accumulated in tap order
+            k = b + o
+            np.add.at(M, (rows, np.clip(k, 0, n - 1)), keys(coords - k))
         return M
 
     Mx = interp_matrix(xs, gx)

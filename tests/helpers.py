@@ -58,3 +58,29 @@ def grad_rel_err(g, ref):
     g = np.asarray(g).reshape(-1, 6)
     ref = np.asarray(ref).reshape(-1, 6)
     return float(np.linalg.norm(g - ref, axis=1).max() / max(np.linalg.norm(ref, axis=1).max(), 1e-300))
+
+
+def view_subset(sc, maps, views):
+    """The scene restricted to `views` (sorted view ids): their records and maps, and the
+    pairs with both ends among them, renumbered.  The first kept view is fixed."""
+    import synth
+    views = np.asarray(sorted(views), dtype=np.int64)
+    new_id = -np.ones(sc.n_views, dtype=np.int64)
+    new_id[views] = np.arange(len(views))
+    keep = (new_id[sc.pairs[:, 0]] >= 0) & (new_id[sc.pairs[:, 1]] >= 0)
+    pairs = new_id[sc.pairs[keep]].astype(np.int32)
+    recs, gts, offs = [], [], [0]
+    for v in views:
+        a, b = sc.rec_off[v], sc.rec_off[v + 1]
+        recs.append(sc.rec[a:b])
+        gts.append(sc.depth_gt_at_rec[a:b])
+        offs.append(offs[-1] + (b - a))
+    fixed = np.zeros(len(views), dtype=np.uint8)
+    fixed[0] = 1
+    T_init = sc.T_init[views].copy()
+    T_init[0] = sc.T_gt[views[0]]
+    sub = synth.Scene(W=sc.W[views], H=sc.H[views], K=sc.K[views], T_gt=sc.T_gt[views], T_init=T_init,
+                      rec_off=np.array(offs, dtype=np.int64), rec=np.concatenate(recs, axis=0),
+                      edges=[sc.edges[v] for v in views], pairs=pairs, fixed=fixed,
+                      scale=synth.scene_scale(sc.T_gt[views]), depth_gt_at_rec=np.concatenate(gts))
+    return sub, [maps[v] for v in views]

@@ -1,0 +1,278 @@
+"""The GPU path on the full-size synthetic workloads, against the FP64 oracle.
+
+  * 32-view 518x392 ring (20k records per view, 8 neighbours): the adjoint kernel's gradient
+    (through the autograd function) against central differences of the objective on 16
+    random poses, and a 200-step optimisation against the oracle's.
+  * 200-view 518x392 walk (30k records per view, 10 neighbours, 6e7 evaluations): loss,
+    gradient and per-pair sums against the oracle; device memory of the recomputing adjoint
+    against what stored per-sample Jacobians would need.
+  * uneven scenes batched in one launch: the graph-captured batched step against each scene
+    stepped alone with the plain per-step launches.
+  * 500-view 518x518 ring in BF16 maps / FP16 depth: kernel parity and precision cost on a
+    50-view subset against the oracle, and the optimisation against the FP32 GPU form and the
+    oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import (bf16_bits, bf16_to_f32, gpu_scene, grad_rel_err, oracle_maps_f32, rot_err_deg,
+                           scene_part, trans_err, view_subset)
+from tests.test_gpu_parity import check_against_oracle, oracle_of, pose4
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA GPU required", allow_module_level=True)
+
+import paper_2607_00579_gb300 as epo  # noqa: E402
+
+FD_H = 1e-9        # rad / scene units: below the spacing of the objective's kinks (see below)
+FD_RTOL = 1e-3     # central-difference truncation (<= 2e-4 here) + the FP32 gradient bound (1e-4)
+
+
+def apply_left(T, v, xi):
+    T = T.copy()
+    T[v] = (pose4(oracle.se3_exp(xi)) @ pose4(T[v]))[:3].reshape(-1)
+    return T
+
+
+def gpu_maps(sc):
+    """Distance fields of every view from the GPU distance-transform kernel (exact, checked
+    against the oracle's EDT by the parity tests)."""
+    return [epo.distance_field(torch.from_numpy(e).cuda()).cpu().numpy() for e in sc.edges]
+
+
+@pytest.fixture(scope="module")
+def ring32():
+    sc = synth.make_scene(synth.RING32_518x392)
+    return sc, oracle_maps_f32(sc)
+
+
+# ---------------------------------------------------------------------------------------------
+def test_ring32_adjoint_gradient_matches_central_differences_on_16_poses(ring32):
+    """The objective is piecewise smooth: a sample's distance has kinks where its projection
+    crosses a bilinear cell line, a medial ridge of the distance field, the border or the
+    clamp, and with 160k samples per pose the kinks are ~1e-6 rad apart.  Central
+    differences in FP64 with h = 1e-9 therefore see the local slope (the GPU's FP32 loss
+    cannot resolve such steps, so the differences are taken of the oracle's objective on the
+    same stored inputs: only the pairs that touch the pose, scaled by their share of the
+    2/P normaliser)."""
+    sc, maps = ring32
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    xi = torch.zeros((sc.n_views, 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    L = epo.EdgeLoss.apply(xi, s)
+    L.sum().backward()
+    g = xi.grad.cpu().numpy()
+    rng = np.random.default_rng(16)
+    views = rng.choice(np.flatnonzero(sc.fixed == 0), 16, replace=False)
+    maps64 = [m.astype(np.float64) for m in maps]
+    fd = np.zeros((16, 6))
+    for n, v in enumerate(views):
+        sel = np.flatnonzero((sc.pairs[:, 0] == v) | (sc.pairs[:, 1] == v))
+        o = oracle.OracleScene(sc.W, sc.H, sc.K, sc.rec_off, sc.rec, maps64, sc.pairs[sel])
+        share = len(sel) / sc.n_pairs
+        for k in range(6):
+            e = np.zeros(6)
+            e[k] = FD_H
+            lp = o.loss_grad(apply_left(sc.T_init, v, e), 10.0)["loss"]
+            lm = o.loss_grad(apply_left(sc.T_init, v, -e), 10.0)["loss"]
+            fd[n, k] = share * (lp - lm) / (2 * FD_H)
+    err = np.linalg.norm(g[views] - fd, axis=1)
+    assert err.max() <= FD_RTOL * np.linalg.norm(fd, axis=1).max(), (err, np.linalg.norm(fd, axis=1))
+    # the fixed view has no gradient through the optimiser, but its objective gradient is real
+    assert np.linalg.norm(g, axis=1).min() > 0
+
+
+def perturbed(T, eps, seed):
+    """Every pose left-multiplied by Exp of an N(0, eps^2) twist (rounding-level nudges)."""
+    rng = np.random.default_rng(seed)
+    for v in range(len(T)):
+        T = apply_left(T, v, rng.normal(0.0, eps, 6))
+    return T
+
+
+def oracle_envelope(o, sc, n_steps, checkpoints, kw, eps=1e-9):
+    """The oracle's optimisation from the initial poses and from the same poses nudged by
+    eps, stepped to each checkpoint.  Adam divides every gradient component by its running
+    RMS, so a component near zero steps by about the full learning rate whichever sign
+    rounding gives it: two runs whose gradients differ at rounding level separate by a
+    fraction of a degree within tens of steps although each step is computed to 1e-16.
+    Returns the unperturbed final poses and the largest separation (degrees, fraction of
+    scene scale) seen at the checkpoints."""
+    A = (sc.T_init.copy(), None, None)
+    B = (perturbed(sc.T_init.copy(), eps, 99), None, None)
+    fixed = sc.fixed
+    B[0][fixed.astype(bool)] = sc.T_init[fixed.astype(bool)]
+    step, sep_r, sep_t, hist = 0, 0.0, 0.0, []
+    for c in checkpoints:
+        Ta, ma, va, ha = o.optimize(A[0], fixed, c - step, step0=step, m=A[1], v=A[2], **kw)
+        Tb, mb, vb, _ = o.optimize(B[0], fixed, c - step, step0=step, m=B[1], v=B[2], **kw)
+        A, B, step = (Ta, ma, va), (Tb, mb, vb), c
+        hist.extend(ha)
+        sep_r = max(sep_r, rot_err_deg(Ta, Tb).max())
+        sep_t = max(sep_t, trans_err(Ta, Tb, sc.scale).max())
+    assert step == n_steps
+    return A[0], sep_r, sep_t, np.array(hist)
+
+
+def test_ring32_200_steps_track_oracle(ring32):
+    """200 steps: the GPU's loss and gradient match the oracle's at the poses the GPU reaches
+    along its trajectory, its final poses lie within the oracle's own rounding-sensitivity
+    envelope, and both reach the same accuracy against the ground truth."""
+    sc, maps = ring32
+    kw = dict(lr_rot=1e-3, lr_trans=1e-2)
+    s = gpu_scene(sc, maps, **kw)
+    s.set_poses(sc.T_init)
+    o = oracle_of(sc, maps)
+    step = 0
+    for c in (50, 100, 150, 200):
+        s.step(c - step)
+        step = c
+        loss, grad = s.loss_and_grad()
+        T = s.get_poses()
+        r = o.loss_grad(T, lam=oracle.lambda_at(step))
+        check_against_oracle(loss[0], grad, r, sc.pairs, T, lam=oracle.lambda_at(step))
+    Tg = s.get_poses()
+    To, sep_r, sep_t, hist = oracle_envelope(o, sc, 200, (50, 100, 150, 200), kw)
+    assert rot_err_deg(Tg, To).max() <= 3.0 * max(sep_r, 0.01)
+    assert trans_err(Tg, To, sc.scale).max() <= 3.0 * max(sep_t, 1e-4)
+    r0, t0 = rot_err_deg(sc.T_init, sc.T_gt).mean(), trans_err(sc.T_init, sc.T_gt, sc.scale).mean()
+    rg, tg = rot_err_deg(Tg, sc.T_gt).mean(), trans_err(Tg, sc.T_gt, sc.scale).mean()
+    ro, to = rot_err_deg(To, sc.T_gt).mean(), trans_err(To, sc.T_gt, sc.scale).mean()
+    assert rg < 0.5 * r0 and tg < 0.5 * t0
+    assert abs(rg - ro) <= 0.05 * ro and abs(tg - to) <= 0.05 * to
+    assert hist[-1] < hist[0]
+    assert s.get_state()[0] == 200
+
+
+# ---------------------------------------------------------------------------------------------
+def test_walk200_loss_grad_matches_oracle_and_adjoint_memory():
+    sc = synth.make_scene(synth.WALK200_518x392)
+    maps = gpu_maps(sc)
+    for v in (0, 99, 199):
+        assert np.array_equal(maps[v], oracle.edt(sc.edges[v]).astype(np.float32))
+    s = gpu_scene(sc, maps)
+    s.set_poses(sc.T_init)
+    evals = s.info().evals_per_step
+    assert evals > 5e7
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=s.pair_stats())
+    # the autograd function (recomputing adjoint) gives the same gradient ...
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    xi = torch.zeros((sc.n_views, 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    L = epo.EdgeLoss.apply(xi, s)
+    L.sum().backward()
+    torch.cuda.synchronize()
+    assert L.item() == pytest.approx(loss[0], rel=1e-12)
+    assert grad_rel_err(xi.grad.cpu().numpy(), grad) < 1e-9
+    # ... without storing per-sample Jacobians: torch allocates O(views) bytes for the
+    # backward, and the library holds the inputs (the maps twice: the row-pitched atlas and
+    # the gather-capable arrays) plus O(pairs + views) state, far below the
+    # evals x (2 x 6 + 2) FP32 a stored-Jacobian variant needs on top of the inputs
+    stored_jacobian = evals * 14 * 4
+    assert torch.cuda.max_memory_allocated() - base < 1 << 20
+    info = s.info()
+    assert info.device_bytes < info.record_bytes + 2.2 * info.map_bytes + (64 << 20)
+    assert info.device_bytes < stored_jacobian / 5
+
+
+# ---------------------------------------------------------------------------------------------
+def test_uneven_batch_graph_step_equals_plain_per_scene_steps():
+    specs = synth.batch64_uneven_specs()[:6]
+    scenes = [synth.make_scene(sp) for sp in specs]
+    maps = [gpu_maps(sc) for sc in scenes]
+    b = epo.Scene([scene_part(sc, m) for sc, m in zip(scenes, maps)])
+    b.set_poses(np.concatenate([sc.T_init for sc in scenes]))
+    lb, gb = b.loss_and_grad()
+    off = 0
+    for k, (sc, m) in enumerate(zip(scenes, maps)):
+        o = oracle_of(sc, m).loss_grad(sc.T_init, lam=10.0)
+        check_against_oracle(lb[k], gb[off:off + sc.n_views], o, sc.pairs, sc.T_init)
+        off += sc.n_views
+    b.step(30)
+    Tb = b.get_poses()
+    off = 0
+    for sc, m in zip(scenes, maps):
+        s = gpu_scene(sc, m)
+        s.set_poses(sc.T_init)
+        s.step_plain(30)
+        s.check()
+        Tp = s.get_poses()
+        Tk = Tb[off:off + sc.n_views]
+        # the same kernels over the same samples: only the order of FP64 atomics differs
+        assert np.abs(Tk - Tp).max() < 1e-7
+        assert rot_err_deg(Tk, sc.T_gt).mean() < rot_err_deg(sc.T_init, sc.T_gt).mean()
+        off += sc.n_views
+
+
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def ring500():
+    sc = synth.make_scene(synth.RING500_518x518)
+    return sc, gpu_maps(sc)
+
+
+def mixed_precision_scene(sc, maps, **kw):
+    return gpu_scene(sc, [bf16_bits(m) for m in maps], rec=synth.records_f16(sc.rec),
+                     record_dtype=epo.EPO_F16, map_dtype=epo.EPO_BF16, **kw)
+
+
+def same_accuracy(Ta, Tb, sc, rel=0.1):
+    """Both pose sets improve on the initial poses, and their mean errors against the ground
+    truth (rotation in degrees, camera centre as a fraction of the scene scale) agree to
+    `rel` of the larger one."""
+    r0, t0 = rot_err_deg(sc.T_init, sc.T_gt).mean(), trans_err(sc.T_init, sc.T_gt, sc.scale).mean()
+    ra, ta = rot_err_deg(Ta, sc.T_gt).mean(), trans_err(Ta, sc.T_gt, sc.scale).mean()
+    rb, tb = rot_err_deg(Tb, sc.T_gt).mean(), trans_err(Tb, sc.T_gt, sc.scale).mean()
+    assert ra < r0 and rb < r0 and ta < t0 and tb < t0, (r0, ra, rb, t0, ta, tb)
+    assert abs(ra - rb) <= rel * max(ra, rb), (ra, rb)
+    assert abs(ta - tb) <= rel * max(ta, tb), (ta, tb)
+
+
+def test_ring500_bf16_fp16_subset_parity_and_precision_cost(ring500):
+    sc_full, maps_full = ring500
+    sc, maps = view_subset(sc_full, maps_full, range(50))
+    kw = dict(lr_rot=1e-3, lr_trans=1e-2)
+    s = mixed_precision_scene(sc, maps, **kw)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    # kernel parity: the oracle sees exactly the stored values
+    o_same = oracle.scene_from_synth(sc, [bf16_to_f32(bf16_bits(m)).astype(np.float64) for m in maps],
+                                     rec=synth.records_f16_widened(sc.rec))
+    check_against_oracle(loss[0], grad, o_same.loss_grad(sc.T_init, lam=10.0), sc.pairs, sc.T_init,
+                         stats=s.pair_stats())
+    # precision cost: the oracle sees the full-precision inputs
+    o_full = oracle_of(sc, maps)
+    r = o_full.loss_grad(sc.T_init, lam=10.0)
+    assert abs(loss[0] - r["loss"]) <= 1e-2 * r["loss"]
+    assert grad_rel_err(grad, r["grad"]) <= 1e-2
+    # the optimisation: kernel parity along the GPU's trajectory, and the same final accuracy
+    # as the oracle on full-precision inputs
+    step = 0
+    for c in (50, 100):
+        s.step(c - step)
+        step = c
+        T = s.get_poses()
+        loss, grad = s.loss_and_grad()
+        check_against_oracle(loss[0], grad, o_same.loss_grad(T, lam=oracle.lambda_at(step)), sc.pairs, T,
+                             lam=oracle.lambda_at(step))
+    To, _, _, _ = o_full.optimize(sc.T_init, sc.fixed, 100, **kw)
+    same_accuracy(s.get_poses(), To, sc)
+
+
+def test_ring500_bf16_fp16_form_tracks_fp32_form(ring500):
+    sc, maps = ring500
+    kw = dict(lr_rot=1e-3, lr_trans=1e-2)
+    a = mixed_precision_scene(sc, maps, **kw)
+    b = gpu_scene(sc, maps, **kw)
+    for s in (a, b):
+        s.set_poses(sc.T_init)
+        s.step(100)
+    same_accuracy(a.get_poses(), b.get_poses(), sc)
