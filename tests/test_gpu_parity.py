@@ -447,3 +447,24 @@ def test_full_size_sampled_pairs_match_oracle(ring32):
     # a fraction of a percent of the samples took the exact path; none overflowed its queue
     queued, overflow = epo._binding.epo_fixup_stats(s.handle)
     assert 0 < queued < 0.05 * s.info().evals_per_step and overflow == 0
+
+
+def test_gather_probe_rates_and_argument_checks():
+    B = epo._binding
+    r = {}
+    for g in (epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX):
+        for pat in (0, 1):
+            for md in (epo.EPO_F32, epo.EPO_BF16):
+                r[g, pat, md] = B.epo_gather_probe(8, 518, 392, md, g, pat, 1 << 22, 3)
+    # a GPU serves between 1e9 and 1e13 footprints per second; warp-coherent positions reuse
+    # cache lines, so they are served at least as fast as scattered ones (within noise)
+    assert all(1e9 < v < 1e13 for v in r.values()), r
+    for g in (epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX):
+        assert r[g, 1, epo.EPO_F32] > 0.8 * r[g, 0, epo.EPO_F32]
+    for bad in [dict(n_maps=0), dict(W=1), dict(pattern=2), dict(gather=0), dict(map_dtype=7),
+                dict(pattern=1, W=40)]:
+        a = dict(n_maps=2, W=64, H=32, map_dtype=epo.EPO_F32, gather=epo.EPO_GATHER_LDG, pattern=0)
+        a.update(bad)
+        with pytest.raises(epo.EpoError) as e:
+            B.epo_gather_probe(a["n_maps"], a["W"], a["H"], a["map_dtype"], a["gather"], a["pattern"], 1000, 1)
+        assert e.value.status == B.EPO_ERR_INVALID_ARG
