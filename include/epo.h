@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define EPO_ABI_VERSION 1
+#define EPO_ABI_VERSION 2
 
 typedef enum {
   EPO_OK = 0,
@@ -107,6 +107,11 @@ typedef struct {
   int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 (two in flight at a time) */
   int32_t grid_blocks;       /* 0 = default (persistent: SMs x resident blocks) */
   int32_t timing;            /* 1: bracket the edge kernel with CUDA events (epo_kernel_time) */
+  int32_t tail_pairs;        /* work items of the last wave (as many as the grid has blocks):
+                                0 = each covers all of its view's pairs, like the others;
+                                n > 0 = split into items of at most n pairs, so that the
+                                blocks finish together; -1 = default (autotuned when
+                                autotune is on, else 0) */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -120,6 +125,7 @@ typedef struct {
   int32_t n_tiles;           /* work items of the persistent kernels */
   int32_t gather, block_threads, records_per_thread, grid_blocks; /* schedule in use */
   int32_t kernels_per_step;  /* kernel launches in one epo_step */
+  int32_t tail_pairs;        /* pairs per work item of the last wave (0 = not split) */
 } epo_scene_info;
 
 /* Defaults: delta 1, lambda 10 -> 6 over 1000 steps, eps_z 1e-6, NORM_VALID,

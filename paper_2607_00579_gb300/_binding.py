@@ -69,7 +69,7 @@ class epo_options(ctypes.Structure):
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
                 ("autotune", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32), ("tail_pairs", ctypes.c_int32)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -79,7 +79,8 @@ class epo_scene_info(ctypes.Structure):
                 ("record_bytes", ctypes.c_int64), ("map_bytes", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("kernels_per_step", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("kernels_per_step", ctypes.c_int32),
+                ("tail_pairs", ctypes.c_int32)]
 
 
 class epo_noalloc_problem(ctypes.Structure):

@@ -76,9 +76,11 @@ struct epo_scene {
   ViewDev* d_views = nullptr;
   TileDev* d_tiles = nullptr;
   int32_t n_tiles = 0;
-  int tiles_for = -1;  // tile size the current table was built for
+  int tiles_for = -1;   // tile size the current table was built for
+  int tiles_tail = -1;  // and its tail split
+  int tail = 0;         // pairs per work item of the last wave (0 = not split)
   struct TileTable {
-    int tile;
+    int tile, tail, grid;
     TileDev* p;
     int32_t n;
   };
@@ -100,6 +102,11 @@ struct epo_scene {
   int64_t* d_step = nullptr;
   int32_t* d_flag = nullptr;
   unsigned int* d_done = nullptr;
+  // loss chunks: 32 consecutive pairs of one scene per pose-kernel block
+  int32_t n_loss_chunks = 0;
+  int32_t *d_loss_chunk_off = nullptr, *d_loss_chunk_scene = nullptr;
+  double* d_loss_part = nullptr;
+  unsigned int* d_scene_done = nullptr;
   int32_t* h_flag = nullptr;  // pinned
   int64_t device_bytes = 0;
   // stage timing events (options.timing): before setup, after setup, after the edge
@@ -185,6 +192,11 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.lambda = S->d_lambda;
   a.flag = S->d_flag;
   a.done = S->d_done;
+  a.n_loss_chunks = S->n_loss_chunks;
+  a.loss_chunk_off = S->d_loss_chunk_off;
+  a.loss_chunk_scene = S->d_loss_chunk_scene;
+  a.loss_part = S->d_loss_part;
+  a.scene_done = S->d_scene_done;
   a.gscale = gscale;
   a.lambda0 = S->opt.lambda0;
   a.lambda1 = S->opt.lambda1;
@@ -199,37 +211,68 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   return a;
 }
 
-epo_status build_tiles(epo_scene* S, int tile) {
-  if (S->tiles_for == tile) return EPO_OK;
+int resident_blocks(epo_scene* S, int gather, int rpt, int block);
+
+// Work items of the edge kernel, in the order the blocks claim them: (view, records
+// [begin, begin + n), pairs [q0, q1) of the view's outgoing pair list).  Each item covers
+// `tile` records and all of the view's pairs, except the last `grid` items (the final wave
+// of a grid of that many blocks), which are split into items of at most `tail` pairs so
+// that the blocks run out of work at nearly the same time.
+epo_status build_tiles(epo_scene* S, int tile, int tail, int grid) {
+  if (S->tiles_for == tile && S->tiles_tail == tail) return EPO_OK;
   S->graph_dirty = true;
   for (const auto& tt : S->tile_tables)
-    if (tt.tile == tile) {
+    if (tt.tile == tile && tt.tail == tail && (tail == 0 || tt.grid == grid)) {
       S->d_tiles = tt.p;
       S->n_tiles = tt.n;
       S->tiles_for = tile;
+      S->tiles_tail = tail;
       return EPO_OK;
     }
   std::vector<TileDev> t;
   for (int v = 0; v < S->n_views; ++v) {
     const ViewDev& vd = S->views[v];
-    if (vd.n_rec == 0 || S->src_pair_off[v + 1] == S->src_pair_off[v]) continue;
+    const int32_t q0 = S->src_pair_off[v], q1 = S->src_pair_off[v + 1];
+    if (vd.n_rec == 0 || q1 == q0) continue;
     for (int64_t b = 0; b < vd.n_rec; b += tile) {
       TileDev td;
       td.view = v;
       td.begin = vd.rec_begin + b;
       td.n = (int32_t)std::min<int64_t>(tile, vd.n_rec - b);
+      td.q0 = q0;
+      td.q1 = q1;
       t.push_back(td);
     }
+  }
+  if (tail > 0 && !t.empty()) {
+    const size_t keep = t.size() > (size_t)grid ? t.size() - (size_t)grid : 0;
+    std::vector<TileDev> u(t.begin(), t.begin() + keep);
+    for (size_t k = keep; k < t.size(); ++k)
+      for (int32_t q = t[k].q0; q < t[k].q1; q += tail) {
+        TileDev td = t[k];
+        td.q0 = q;
+        td.q1 = std::min(q + tail, t[k].q1);
+        u.push_back(td);
+      }
+    t.swap(u);
   }
   TileDev* d = nullptr;
   ALLOC(d, t.size());
   if (!t.empty()) CK(cudaMemcpy(d, t.data(), t.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
-  S->tile_tables.push_back({tile, d, (int32_t)t.size()});
+  S->tile_tables.push_back({tile, tail, grid, d, (int32_t)t.size()});
   S->d_tiles = d;
   S->n_tiles = (int32_t)t.size();
   S->tiles_for = tile;
+  S->tiles_tail = tail;
   return EPO_OK;
 }
+
+// The work items of the current schedule.
+epo_status build_tiles(epo_scene* S, int gather, int rpt, int block, int tail) {
+  return build_tiles(S, block * rpt, tail, tail ? resident_blocks(S, gather, rpt, block) : 0);
+}
+
+epo_status build_tiles(epo_scene* S) { return build_tiles(S, S->gather, S->rpt, S->block, S->tail); }
 
 EdgeArgs edge_args(epo_scene* S) {
   EdgeArgs a;
@@ -259,17 +302,22 @@ EdgeArgs edge_args(epo_scene* S) {
   return a;
 }
 
-int grid_for(epo_scene* S, int gather, int rpt, int block) {
+// Blocks of the persistent edge kernel: every SM holds as many as its registers, threads
+// and shared memory allow (or the caller's fixed grid size).
+int resident_blocks(epo_scene* S, int gather, int rpt, int block) {
   if (S->opt.grid_blocks > 0) return S->opt.grid_blocks;
-  // persistent grid: every SM holds as many blocks as its registers and threads allow
   int per_sm = 0;
   const void* k = edge_kernel_ptr(MODE_FUSED, S->rec_dtype, S->map_dtype, gather, rpt);
   const size_t smem = edge_smem_bytes(rpt, block, S->max_pairs);
   if (smem > 48 * 1024 && k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess || per_sm < 1)
     per_sm = std::max(1, 1024 / block);
-  const int g = S->sm_count * per_sm;
-  return std::max(1, std::min(g, std::max(S->n_tiles, 1)));
+  return std::max(1, S->sm_count * per_sm);
+}
+
+// Launch size of the edge kernel for the current tile table.
+int grid_for(epo_scene* S, int gather, int rpt, int block) {
+  return std::max(1, std::min(resident_blocks(S, gather, rpt, block), std::max(S->n_tiles, 1)));
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -295,10 +343,10 @@ epo_status mark(epo_scene* S, int k, cudaStream_t s) {
     if (m_ != EPO_OK) return m_;           \
   } while (0)
 
-epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, cudaStream_t s) {
+epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, int tail, cudaStream_t s) {
   if (!schedule_fits(S, rpt, block))
     return fail(S, EPO_ERR_INVALID_ARG, "schedule needs more shared memory than a block has");
-  epo_status st = build_tiles(S, block * rpt);
+  epo_status st = build_tiles(S, gather, rpt, block, tail);
   if (st != EPO_OK) return st;
   EdgeArgs ea = edge_args(S);
   int grid = grid_for(S, gather, rpt, block);
@@ -313,7 +361,7 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
   MARK(0, s);
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
-  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, s);
+  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 1, s));
   MARK(3, s);
@@ -327,7 +375,7 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   MARK(0, s);
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
-  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, s);
+  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 2, s));
   MARK(3, s);
@@ -336,7 +384,7 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
 
 epo_status ensure_graph(epo_scene* S) {
   // build the tile table outside capture (it allocates)
-  epo_status st = build_tiles(S, S->block * S->rpt);
+  epo_status st = build_tiles(S);
   if (st != EPO_OK) return st;
   if (!S->graph_dirty && S->graph) return EPO_OK;
   if (S->graph) {
@@ -381,6 +429,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 1, 2 or 4");
   if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
+  if (o.tail_pairs < -1) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs must be -1, 0 or positive");
   S->stream = (cudaStream_t)cuda_stream;
   const int rec_dtype = descs[0].record_dtype, map_dtype = descs[0].map_dtype;
   if (rec_dtype != EPO_F32 && rec_dtype != EPO_F16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown record dtype");
@@ -563,6 +612,18 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_step, 1);
     ALLOC(S->d_flag, 1);
     ALLOC(S->d_done, 1);
+    std::vector<int32_t> chunk_off(1, 0), chunk_scene;
+    for (int sc = 0; sc < n_scenes; ++sc) {
+      const int32_t np_s = S->scene_pair_off[sc + 1] - S->scene_pair_off[sc];
+      const int32_t nc = (np_s + kLossChunk - 1) / kLossChunk;
+      for (int32_t c = 0; c < nc; ++c) chunk_scene.push_back(sc);
+      chunk_off.push_back(chunk_off.back() + nc);
+    }
+    S->n_loss_chunks = chunk_off.back();
+    ALLOC(S->d_loss_chunk_off, n_scenes + 1);
+    ALLOC(S->d_loss_chunk_scene, chunk_scene.size());
+    ALLOC(S->d_loss_part, chunk_scene.size());
+    ALLOC(S->d_scene_done, n_scenes);
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
     cudaStream_t st = S->stream;
     if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
@@ -620,6 +681,11 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     CK(cudaMemsetAsync(S->d_step, 0, 8, st));
     CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
     CK(cudaMemsetAsync(S->d_done, 0, 4, st));
+    CK(cudaMemsetAsync(S->d_scene_done, 0, 4 * (size_t)n_scenes, st));
+    CK(cudaMemcpyAsync(S->d_loss_chunk_off, chunk_off.data(), chunk_off.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!chunk_scene.empty())
+      CK(cudaMemcpyAsync(S->d_loss_chunk_scene, chunk_scene.data(), chunk_scene.size() * 4, cudaMemcpyHostToDevice,
+                         st));
     CK(cudaMemsetAsync(S->d_pair_acc, 0, (size_t)kAcc * np * 8, st));
     // validate maps on the device
     CK(launch_map_check(S->d_map, S->map_dtype, S->map_elems, S->d_flag, st));
@@ -662,7 +728,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     S->rpt = o.records_per_thread ? o.records_per_thread : 2;
     S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG;
     if (!schedule_fits(S, S->rpt, S->block)) S->block = 128;
-    epo_status bs = build_tiles(S, S->block * S->rpt);
+    S->tail = o.tail_pairs > 0 ? o.tail_pairs : 0;
+    epo_status bs = build_tiles(S);
     if (bs != EPO_OK) return bs;
     CK(cudaStreamSynchronize(st));
   }
@@ -706,6 +773,7 @@ void epo_default_options(epo_options* o) {
   o->adam_eps = 1e-12;
   o->autotune = 0;
   o->gather = EPO_GATHER_AUTO;
+  o->tail_pairs = -1;
 }
 
 int32_t epo_abi_version(void) { return EPO_ABI_VERSION; }
@@ -756,6 +824,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
   info->kernels_per_step = 3;
+  info->tail_pairs = S->tail;
   return EPO_OK;
 }
 
@@ -855,7 +924,7 @@ epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev
   MARK(0, S->stream);
   CK(launch_pair_setup(a, MODE_FWD, S->stream));
   MARK(1, S->stream);
-  st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->stream);
+  st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, S->stream);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 0, S->stream));
   MARK(3, S->stream);
@@ -871,7 +940,7 @@ epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* d
   MARK(0, S->stream);
   CK(launch_pair_setup(a, MODE_BWD, S->stream));
   MARK(1, S->stream);
-  epo_status st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->stream);
+  epo_status st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, S->stream);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 1, S->stream));
   MARK(3, S->stream);
@@ -976,15 +1045,17 @@ epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
 // different candidates are interleaved (one launch of each per pass), so that clock or
 // thermal drift during tuning affects all of them alike, and each candidate is judged by
 // the median of its launches. A first pass over all candidates (3 timed launches each)
-// keeps the 4 best; 12 further passes decide between those.
+// keeps the 4 best; with tail_pairs = -1 each of those is also tried with its last wave
+// split into items of 2 pairs and of 1 pair, and 12 further passes decide.
 epo_status epo_autotune(epo_scene_t S) {
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   S->tuned = true;  // also guards against recursion through maybe_autotune
   struct Cand {
-    int g, r, b;
+    int g, r, b, t;
     std::vector<float> ms;
     float med;
   };
+  const int tail0 = S->opt.tail_pairs > 0 ? S->opt.tail_pairs : 0;
   std::vector<Cand> cands;
   for (int g : {GATHER_LDG, GATHER_TEX})
     for (int r : {1, 2, 4})
@@ -992,7 +1063,7 @@ epo_status epo_autotune(epo_scene_t S) {
         if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
         if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
         if (!schedule_fits(S, r, b)) continue;
-        cands.push_back({g, r, b, {}, 0.f});
+        cands.push_back({g, r, b, tail0, {}, 0.f});
       }
   if (cands.empty()) return fail(S, EPO_ERR_INVALID_ARG, "no edge-kernel schedule fits this scene");
   cudaEvent_t e0, e1;
@@ -1013,7 +1084,7 @@ epo_status epo_autotune(epo_scene_t S) {
   int fill = 0;
   // one launch of candidate c; its time is appended when `timed`
   auto launch = [&](Cand& c, bool timed) -> epo_status {
-    epo_status st = build_tiles(S, c.b * c.r);  // outside the timed interval
+    epo_status st = build_tiles(S, c.g, c.r, c.b, c.t);  // outside the timed interval
     if (st != EPO_OK) return st;
     if (flush) {
       CK(cudaMemsetAsync(flush, ++fill & 0xff, flush_bytes, S->stream));
@@ -1022,7 +1093,7 @@ epo_status epo_autotune(epo_scene_t S) {
     }
     CK(launch_pair_setup(a, MODE_FUSED, S->stream));
     CK(cudaEventRecord(e0, S->stream));
-    st = run_edge(S, MODE_FUSED, c.g, c.r, c.b, S->stream);
+    st = run_edge(S, MODE_FUSED, c.g, c.r, c.b, c.t, S->stream);
     if (st != EPO_OK) return st;
     CK(cudaEventRecord(e1, S->stream));
     CK(cudaEventSynchronize(e1));
@@ -1046,6 +1117,17 @@ epo_status epo_autotune(epo_scene_t S) {
     for (auto& c : cands) c.med = median(c.ms);
     std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.med < y.med; });
     if (cands.size() > 4) cands.resize(4);
+    if (S->opt.tail_pairs == -1) {
+      const size_t n4 = cands.size();
+      for (size_t k = 0; k < n4; ++k)
+        for (int t : {2, 1}) {
+          Cand c = cands[k];
+          c.t = t;
+          c.ms.clear();
+          cands.push_back(c);
+        }
+      for (size_t k = n4; k < cands.size() && st == EPO_OK; ++k) st = launch(cands[k], false);  // warm-up
+    }
     for (int pass = 0; pass < 12 && st == EPO_OK; ++pass)
       for (auto& c : cands)
         if ((st = launch(c, true)) != EPO_OK) break;
@@ -1065,8 +1147,9 @@ epo_status epo_autotune(epo_scene_t S) {
   S->gather = best->g;
   S->rpt = best->r;
   S->block = best->b;
+  S->tail = best->t;
   S->graph_dirty = true;
-  return build_tiles(S, S->block * S->rpt);
+  return build_tiles(S);
 }
 
 epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, float* map_dev,

@@ -1,0 +1,479 @@
+// The edge kernel (sm_103a), steps a2-a7 of one optimisation step.
+//
+//   k_edge   persistent, work = (source view, tile of edge records).  Each thread lifts its
+//            records once (the split projection of Algorithm 2: lift once per image,
+//            project into every paired view), then for every outgoing pair i -> j:
+//            transform, project (Eq. 8), gather the 2x2 footprint of DTF_j, bilinear value
+//            and slope, clamp + Huber (Eq. 7), the adjoint 6-vector, and a warp-shuffle +
+//            block reduction ending in one FP64 atomic per block per pair slot (the
+//            in-kernel per-pair reduction of the fused ProjectSampleHuber kernel,
+//            Appendix A.2).  A sample whose FP32 position lies within its own rounding-error
+//            bound of a discontinuity of the objective (a bilinear cell line, the image
+//            border, the depth threshold, the clamp) is not accumulated but kept in a
+//            shared-memory buffer; the block re-evaluates those samples with every decision
+//            (validity, cell, clamp) taken in FP64, so the GPU objective takes exactly the
+//            branch an FP64 evaluation takes.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "epo_internal.cuh"
+
+namespace epo {
+
+// ------------------------------------------------------------------------------------
+// a2-a7: the edge kernel
+// ------------------------------------------------------------------------------------
+template <int REC>
+__device__ __forceinline__ void load_record(const void* base, int64_t idx, float& u, float& v,
+                                            float& z) {
+  if (REC == 0) {  // EPO_F32: {u, v, z, 0}
+    float4 r = __ldg(reinterpret_cast<const float4*>(base) + idx);
+    u = r.x; v = r.y; z = r.z;
+  } else {         // EPO_F16: {u16 u, u16 v, f16 z, u16 0}
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    u = (float)(r.x & 0xffffu);
+    v = (float)(r.x >> 16);
+    z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+  }
+}
+
+
+// 2x2 footprint (x0, y0) .. (x0+1, y0+1) of a map.
+template <int MAP, int GATHER>
+__device__ __forceinline__ void taps(const void* map, int64_t off, int pitch, unsigned long long tex,
+                                     int x0, int y0, float& m00, float& m01, float& m10, float& m11) {
+  if (GATHER == GATHER_TEX) {
+    // tex2Dgather at the centre of the 2x2 block returns it as (x: (x0, y0+1), y: (x0+1, y0+1),
+    // z: (x0+1, y0), w: (x0, y0)); unnormalised coordinates, point fetch, no filtering.
+    float fx = (float)x0 + 1.0f, fy = (float)y0 + 1.0f;
+    if (MAP == 0) {
+      float4 g = tex2Dgather<float4>((cudaTextureObject_t)tex, fx, fy, 0);
+      m00 = g.w; m01 = g.z; m10 = g.x; m11 = g.y;
+    } else {
+      ushort4 g = tex2Dgather<ushort4>((cudaTextureObject_t)tex, fx, fy, 0);
+      m00 = bf16_bits_to_float(g.w); m01 = bf16_bits_to_float(g.z);
+      m10 = bf16_bits_to_float(g.x); m11 = bf16_bits_to_float(g.y);
+    }
+  } else {
+    if (MAP == 0) {
+      const float* m = reinterpret_cast<const float*>(map) + off + (int64_t)y0 * pitch + x0;
+      m00 = __ldg(m); m01 = __ldg(m + 1); m10 = __ldg(m + pitch); m11 = __ldg(m + pitch + 1);
+    } else {
+      const unsigned short* m = reinterpret_cast<const unsigned short*>(map) + off + (int64_t)y0 * pitch + x0;
+      m00 = bf16_bits_to_float(__ldg(m)); m01 = bf16_bits_to_float(__ldg(m + 1));
+      m10 = bf16_bits_to_float(__ldg(m + pitch)); m11 = bf16_bits_to_float(__ldg(m + pitch + 1));
+    }
+  }
+}
+
+// rcp.approx: |rel. error| <= 2^-23 (PTX ISA), folded into the position error bound
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Butterfly reduce-scatter of 8 per-lane values over a warp: afterwards lane L holds the
+// warp sum of value index slot(L) = (L&1)*4 + ((L>>1)&1)*2 + ((L>>2)&1).
+__device__ __forceinline__ float warp_reduce_scatter8(float v[8], int lane) {
+  const bool b0 = lane & 1, b1 = lane & 2, b2 = lane & 4;
+  float k4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b0 ? v[4 + i] : v[i];
+    const float send = b0 ? v[i] : v[4 + i];
+    k4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+  float k2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b1 ? k4[2 + i] : k4[i];
+    const float send = b1 ? k4[i] : k4[2 + i];
+    k2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  const float keep = b2 ? k2[1] : k2[0];
+  const float send = b2 ? k2[0] : k2[1];
+  float s = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 8);
+  s += __shfl_xor_sync(0xffffffffu, s, 16);
+  return s;
+}
+
+__device__ __forceinline__ int scatter_slot(int lane) {
+  return (lane & 1) * 4 + ((lane >> 1) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// A sample whose FP32 decisions its rounding-error bound cannot settle: its raw record and
+// pair, kept in shared memory until the block re-evaluates it with FP64 decisions.
+struct AmbEntry {
+  float u, v, z;
+  int p;
+};
+constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
+
+// The exact path: lift, transform and project in FP64, take the validity, cell and clamp
+// decisions in FP64 (so the branch is the one an FP64 evaluation takes); the value and the
+// slope terms are smooth given those decisions and are formed in FP32.  Adds straight to
+// the pair's FP64 accumulators.
+template <int MODE, int MAP>
+__device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, float lamf) {
+  const int p = en.p;
+  const int i = a.pair_src[p];
+  const PairParam& P = a.pp[p];
+  const double* Ki = a.K64 + 6 * (size_t)i;
+  const double* Kj = a.K64 + 6 * (size_t)a.pair_dst[p];
+  // K64 holds fx, fy, cx, cy followed by 1/fx, 1/fy
+  const double X[3] = {((double)en.u - Ki[2]) * Ki[4] * (double)en.z, ((double)en.v - Ki[3]) * Ki[5] * (double)en.z,
+                       (double)en.z};
+  const double* R = a.pp64 + 12 * (size_t)p;
+  double Y[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) Y[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + R[9 + r];
+  if (!(Y[2] > (double)a.eps_z)) return;
+  const double iz = __drcp_rn(Y[2]);
+  const double up = Kj[0] * Y[0] * iz + Kj[2];
+  const double vp = Kj[1] * Y[1] * iz + Kj[3];
+  if (!(up >= 0.0 && up <= (double)(P.W - 1) && vp >= 0.0 && vp <= (double)(P.H - 1))) return;
+  const int x0 = min((int)floor(up), P.W - 2);
+  const int y0 = min((int)floor(vp), P.H - 2);
+  const double ca = up - (double)x0, cb = vp - (double)y0;
+  float f00, f01, f10, f11;
+  taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, x0, y0, f00, f01, f10, f11);
+  const double d = (1.0 - ca) * (1.0 - cb) * f00 + ca * (1.0 - cb) * f01 + (1.0 - ca) * cb * f10 + ca * cb * f11;
+  const bool pass = d <= lam;  // clamp decision in FP64
+  const float delta = a.delta;
+  const float df = (float)d, caf = (float)ca, cbf = (float)cb;
+  const float dh = pass ? df : lamf;
+  const float adh = fabsf(dh);
+  const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
+  double* acc = a.pair_acc + (size_t)kAcc * p;
+  if constexpr (MODE != MODE_BWD) {
+    atomicAdd(acc + 0, (double)rho);
+    atomicAdd(acc + 1, 1.0);
+  }
+  if constexpr (MODE != MODE_FWD) {
+    const float drho = pass ? (fabsf(df) <= delta ? df : copysignf(delta, df)) : 0.f;
+    if (drho != 0.f) {
+      const float ddu = (1.f - cbf) * (f01 - f00) + cbf * (f11 - f10);
+      const float ddv = (1.f - caf) * (f10 - f00) + caf * (f11 - f01);
+      const float y0f = (float)Y[0], y1f = (float)Y[1], y2f = (float)Y[2];
+      const float izf = (float)iz;
+      const float gx = drho * ddu * P.fx * izf;
+      const float gy = drho * ddv * P.fy * izf;
+      const float gz = -(gx * y0f + gy * y1f) * izf;
+      atomicAdd(acc + 2, (double)gx);
+      atomicAdd(acc + 3, (double)gy);
+      atomicAdd(acc + 4, (double)gz);
+      atomicAdd(acc + 5, (double)(y1f * gz - y2f * gy));
+      atomicAdd(acc + 6, (double)(y2f * gx - y0f * gz));
+      atomicAdd(acc + 7, (double)(y0f * gy - y1f * gx));
+    }
+  }
+}
+
+template <int MODE, int REC, int MAP, int GATHER, int RPT>
+__global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
+  // dynamic shared memory: lifted records of the tile, their raw (u, v), then every warp's
+  // partial sums per pair of the tile (summed in a fixed warp order at the flush, so the
+  // result does not depend on warp timing)
+  extern __shared__ float4 s_dyn[];
+  float4* s_X = s_dyn;                                                    // [blockDim * RPT]
+  float2* s_UV = reinterpret_cast<float2*>(s_dyn + blockDim.x * RPT);    // [blockDim * RPT]
+  float* s_part = reinterpret_cast<float*>(s_UV + blockDim.x * RPT);     // [warps][max_pairs][8]
+  __shared__ int s_tile, s_next;
+  __shared__ int s_amb_n;
+  __shared__ AmbEntry s_amb[kAmbCap];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+  const unsigned lanemask_lt = (1u << lane) - 1u;
+  const float lam = (float)(*a.lambda);
+  const float delta = a.delta;
+  const float eps_z = a.eps_z;
+  const double lam64 = *a.lambda;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(a.tile_counter, 1);
+    s_amb_n = 0;
+  }
+  __syncthreads();
+  while (s_tile < a.n_tiles) {
+    const int t = s_tile;
+    // claim the next tile now: the atomic's round trip overlaps this tile's work
+    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_counter, 1);
+    const TileDev td = a.tiles[t];
+    const ViewDev vi = a.views[td.view];
+    // a2: stream the tile's records (coalesced 128-bit loads), lift once per record into
+    // shared memory; each thread reads back only its own records
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int idx = threadIdx.x + r * blockDim.x;
+      float u = 0.f, v = 0.f, z = 0.f;
+      if (idx < td.n) load_record<REC>(a.rec, td.begin + idx, u, v, z);
+      const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
+      // rounding-error bound of Y = R X + t: 6u|X|_1 (rotation, lift and FMA roundings);
+      // a record past the tile end gets w < 0 and is skipped
+      const float XA = idx < td.n ? 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
+      s_X[idx] = make_float4(X0, X1, z, XA);
+      s_UV[idx] = make_float2(u, v);
+    }
+    // the item's pair range, loaded where it is needed (holding the whole item in
+    // registers across the pair loop costs a block per SM)
+    const int pb = __ldg(&a.tiles[t].q0);
+    const int pe = __ldg(&a.tiles[t].q1);
+    for (int q = pb; q < pe; ++q) {
+      const int p = a.src_pair_ids[q];
+      if (!a.pair_active[p]) continue;  // uniform over the block
+      const PairParam P = a.pp[p];
+      const float Wm1 = (float)(P.W - 1), Hm1 = (float)(P.H - 1);
+      float acc[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+      // the thread's RPT records, ILP of them in flight at a time: one reduction per pair
+      // for all RPT samples, registers for only ILP
+      constexpr int ILP = RPT < 2 ? RPT : 2;
+#pragma unroll
+      for (int g = 0; g < RPT; g += ILP) {
+        // phase A: project every sample and take the decisions the FP32 bound allows
+        float Y0[ILP], Y1[ILP], Y2[ILP], iz[ILP], up[ILP], vp[ILP], tu[ILP], tv[ILP];
+        bool ok[ILP], amb[ILP];
+        int x0[ILP], y0[ILP];
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
+          Y0[r] = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
+          Y1[r] = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
+          Y2[r] = fmaf(P.r[6], X.x, fmaf(P.r[7], X.y, fmaf(P.r[8], X.z, P.t[2])));
+          const float E = X.w + P.Et;  // |Y_k - Y_k(exact)| <= E
+          const bool front = (X.w >= 0.f) && (Y2[r] > eps_z - E);
+          iz[r] = front ? rcp_approx(Y2[r]) : 0.f;
+          const float xn = Y0[r] * iz[r], yn = Y1[r] * iz[r];
+          up[r] = fmaf(P.fx, xn, P.cx);
+          vp[r] = fmaf(P.fy, yn, P.cy);
+          const float Eiz = E * iz[r];
+          tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn), Eiz), P.cu);  // bound on |u' - u'(exact)|
+          tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn), Eiz), P.cv);
+          const bool cand = front && (fabsf(up[r] - P.hw) <= P.hw + tu[r]) && (fabsf(vp[r] - P.hh) <= P.hh + tv[r]);
+          // within the bound of an integer coordinate (cell lines and the border are integers)
+          // or of the depth threshold: the branch taken must come from the exact evaluation
+          amb[r] = cand && (fabsf(up[r] - rintf(up[r])) <= tu[r] || fabsf(vp[r] - rintf(vp[r])) <= tv[r] ||
+                            fabsf(Y2[r] - eps_z) <= E);
+          ok[r] = cand && !amb[r];
+          // cell of a valid sample: ok implies tu < u' < W-1-tu, so floor(u') is in [0, W-2];
+          // the unsigned range check keeps every gather inside the map regardless
+          x0[r] = __float2int_rd(up[r]);
+          y0[r] = __float2int_rd(vp[r]);
+          if (ok[r] && !((unsigned)x0[r] <= (unsigned)(P.W - 2) && (unsigned)y0[r] <= (unsigned)(P.H - 2))) {
+            ok[r] = false;
+            amb[r] = true;
+          }
+        }
+        // phase B: all gathers in flight together
+        float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          if (ok[r]) {
+            taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, x0[r], y0[r], m00[r], m01[r], m10[r], m11[r]);
+          } else {
+            m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
+          }
+        }
+        // phase C: bilinear value and slope, clamp, robust penalty, adjoint
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float ca = up[r] - (float)x0[r];
+          const float cb = vp[r] - (float)y0[r];
+          const float top = fmaf(ca, m01[r] - m00[r], m00[r]);
+          const float bot = fmaf(ca, m11[r] - m10[r], m10[r]);
+          float d = fmaf(cb, bot - top, top);
+          float ddu = fmaf(cb, (m11[r] - m10[r]) - (m01[r] - m00[r]), m01[r] - m00[r]);
+          float ddv = bot - top;
+          if (ok[r]) {
+            // the clamp is a discontinuity of the slope term: same treatment
+            const float td = fmaf(tu[r], fabsf(ddu), fmaf(tv[r], fabsf(ddv), 8.f * kU32 * (fabsf(d) + 1.f)));
+            if (fabsf(d - lam) <= td) {
+              ok[r] = false;
+              amb[r] = true;
+            }
+          }
+          // keep the ambiguous samples for the exact path (warp-aggregated append)
+          const unsigned bal = __ballot_sync(0xffffffffu, amb[r]);
+          if (bal) {
+            const int leader = __ffs(bal) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (amb[r]) {
+              const int pos = base + __popc(bal & lanemask_lt);
+              if (pos < kAmbCap) {
+                const int li = threadIdx.x + (g + r) * blockDim.x;
+                const float2 uv = s_UV[li];
+                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
+              } else {
+                // buffer full: evaluate this sample with FP32 decisions instead
+                atomicAdd(a.q_overflow, 1u);
+                ok[r] = (Y2[r] > eps_z) && (up[r] >= 0.f) && (up[r] <= Wm1) && (vp[r] >= 0.f) && (vp[r] <= Hm1);
+                if (ok[r]) {
+                  const int fx0 = min(max(x0[r], 0), P.W - 2), fy0 = min(max(y0[r], 0), P.H - 2);
+                  const float fa = up[r] - (float)fx0, fb = vp[r] - (float)fy0;
+                  float n00, n01, n10, n11;
+                  taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, fx0, fy0, n00, n01, n10, n11);
+                  const float t2 = fmaf(fa, n01 - n00, n00);
+                  const float b2 = fmaf(fa, n11 - n10, n10);
+                  d = fmaf(fb, b2 - t2, t2);
+                  ddu = fmaf(fb, (n11 - n10) - (n01 - n00), n01 - n00);
+                  ddv = b2 - t2;
+                }
+              }
+            }
+          }
+          if (ok[r]) {
+            // a5: clamp + Huber
+            const float dh = fminf(d, lam);
+            const float adh = fabsf(dh);
+            const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
+            if constexpr (MODE != MODE_BWD) {
+              acc[0] += rho;
+              acc[1] += 1.f;
+            }
+            if constexpr (MODE != MODE_FWD) {
+              // a6: adjoint in camera-j coordinates
+              const float drho = d <= lam ? (fabsf(d) <= delta ? d : copysignf(delta, d)) : 0.f;
+              const float gx = drho * ddu * P.fx * iz[r];
+              const float gy = drho * ddv * P.fy * iz[r];
+              const float gz = -(gx * Y0[r] + gy * Y1[r]) * iz[r];
+              acc[2] += gx;
+              acc[3] += gy;
+              acc[4] += gz;
+              acc[5] += Y1[r] * gz - Y2[r] * gy;
+              acc[6] += Y2[r] * gx - Y0[r] * gz;
+              acc[7] += Y0[r] * gy - Y1[r] * gx;
+            }
+          }
+        }
+      }
+      // a7: warp reduce-scatter; lanes 0..7 store the warp's 8 sums (no block barrier)
+      const float sred = warp_reduce_scatter8(acc, lane);
+      if (lane < 8) s_part[((size_t)warp * a.max_pairs + (q - pb)) * kAcc + scatter_slot(lane)] = sred;
+    }
+    __syncthreads();  // every warp has stored its partial sums for this tile
+    // flush: warps summed in a fixed order, one FP64 atomic per used pair slot
+    constexpr int S0 = MODE == MODE_BWD ? 2 : 0;
+    constexpr int NS = MODE == MODE_FWD ? 2 : (MODE == MODE_BWD ? 6 : 8);
+    const int nq = (pe - pb) * NS;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+      const int qq = k / NS, slot = S0 + k % NS;
+      const int p = a.src_pair_ids[pb + qq];
+      if (!a.pair_active[p]) continue;
+      float s = 0.f;
+      for (int w = 0; w < nwarp; ++w) s += s_part[((size_t)w * a.max_pairs + qq) * kAcc + slot];
+      if (s != 0.f) atomicAdd(a.pair_acc + (size_t)kAcc * p + slot, (double)s);
+    }
+    if (threadIdx.x == 0) s_tile = s_next;
+    __syncthreads();
+    // exact path: when the buffer is more than half full, and once more before exiting
+    const int n_amb = min(s_amb_n, kAmbCap);
+    if (n_amb > (s_tile < a.n_tiles ? kAmbCap / 2 : 0)) {
+      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, MAP>(a, s_amb[k], lam64, lam);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        atomicAdd(a.q_count, (unsigned)n_amb);
+        s_amb_n = 0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+size_t edge_smem_bytes(int rpt, int block, int max_pairs) {
+  // dynamic part: lifted records, raw (u, v), per-warp per-pair partial sums
+  return sizeof(float4) * (size_t)rpt * block + sizeof(float2) * (size_t)rpt * block +
+         sizeof(float) * kAcc * (size_t)max_pairs * (block / 32);
+}
+
+template <int MODE, int REC, int MAP, int GATHER, int R>
+static cudaError_t launch_edge_one(const EdgeArgs& a, int block, int grid, cudaStream_t s) {
+  const size_t smem = edge_smem_bytes(R, block, a.max_pairs);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_edge<MODE, REC, MAP, GATHER, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_edge<MODE, REC, MAP, GATHER, R><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int REC, int MAP, int GATHER>
+static cudaError_t launch_edge_rpt(const EdgeArgs& a, int rpt, int block, int grid, cudaStream_t s) {
+  switch (rpt) {
+    case 1: return launch_edge_one<MODE, REC, MAP, GATHER, 1>(a, block, grid, s);
+    case 2: return launch_edge_one<MODE, REC, MAP, GATHER, 2>(a, block, grid, s);
+    case 4: return launch_edge_one<MODE, REC, MAP, GATHER, 4>(a, block, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int MODE, int REC, int MAP>
+static cudaError_t launch_edge_g(const EdgeArgs& a, int gather, int rpt, int block, int grid,
+                                 cudaStream_t s) {
+  if (gather == GATHER_TEX) return launch_edge_rpt<MODE, REC, MAP, GATHER_TEX>(a, rpt, block, grid, s);
+  return launch_edge_rpt<MODE, REC, MAP, GATHER_LDG>(a, rpt, block, grid, s);
+}
+
+template <int MODE>
+static cudaError_t launch_edge_m(const EdgeArgs& a, int rec, int map, int gather, int rpt, int block,
+                                 int grid, cudaStream_t s) {
+  if (rec == 0 && map == 0) return launch_edge_g<MODE, 0, 0>(a, gather, rpt, block, grid, s);
+  if (rec == 0 && map == 1) return launch_edge_g<MODE, 0, 1>(a, gather, rpt, block, grid, s);
+  if (rec == 1 && map == 0) return launch_edge_g<MODE, 1, 0>(a, gather, rpt, block, grid, s);
+  return launch_edge_g<MODE, 1, 1>(a, gather, rpt, block, grid, s);
+}
+
+// rec_dtype: 0 = f32 records, 1 = f16-depth records; map_dtype: 0 = f32, 1 = bf16.
+cudaError_t launch_edge(const EdgeArgs& a, int mode, int rec_dtype, int map_dtype, int gather,
+                        int rpt, int block, int grid, cudaStream_t s) {
+  if (a.n_tiles == 0) return cudaSuccess;
+  switch (mode) {
+    case MODE_FWD: return launch_edge_m<MODE_FWD>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+    case MODE_BWD: return launch_edge_m<MODE_BWD>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+    default: return launch_edge_m<MODE_FUSED>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+  }
+}
+
+template <int MODE, int REC, int MAP, int GATHER>
+static const void* edge_ptr_rpt(int rpt) {
+  switch (rpt) {
+    case 1: return (const void*)k_edge<MODE, REC, MAP, GATHER, 1>;
+    case 2: return (const void*)k_edge<MODE, REC, MAP, GATHER, 2>;
+    case 4: return (const void*)k_edge<MODE, REC, MAP, GATHER, 4>;
+    default: return nullptr;
+  }
+}
+
+template <int MODE>
+static const void* edge_ptr_m(int rec, int map, int gather, int rpt) {
+  if (gather == GATHER_TEX) {
+    if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_TEX>(rpt);
+    if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_TEX>(rpt);
+    if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_TEX>(rpt);
+    return edge_ptr_rpt<MODE, 1, 1, GATHER_TEX>(rpt);
+  }
+  if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_LDG>(rpt);
+  if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_LDG>(rpt);
+  if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_LDG>(rpt);
+  return edge_ptr_rpt<MODE, 1, 1, GATHER_LDG>(rpt);
+}
+
+const void* edge_kernel_ptr(int mode, int rec_dtype, int map_dtype, int gather, int rpt) {
+  switch (mode) {
+    case MODE_FWD: return edge_ptr_m<MODE_FWD>(rec_dtype, map_dtype, gather, rpt);
+    case MODE_BWD: return edge_ptr_m<MODE_BWD>(rec_dtype, map_dtype, gather, rpt);
+    default: return edge_ptr_m<MODE_FUSED>(rec_dtype, map_dtype, gather, rpt);
+  }
+}
+
+}  // namespace epo

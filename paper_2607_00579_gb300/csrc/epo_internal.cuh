@@ -26,7 +26,13 @@
 
 namespace epo {
 
-constexpr int kAcc = 8;  // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
+// unit roundoff of binary32
+constexpr float kU32 = 5.9604645e-08f;
+
+__device__ __forceinline__ float bf16_bits_to_float(unsigned int b) { return __uint_as_float(b << 16); }
+
+constexpr int kAcc = 8;
+constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)  // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
 
 enum Mode { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2 };
 enum Gather { GATHER_LDG = 1, GATHER_TEX = 2 };
@@ -46,6 +52,7 @@ struct TileDev {
   int32_t view;
   int32_t n;        // records in this tile
   int64_t begin;    // first record
+  int32_t q0, q1;   // pairs [q0, q1) of the view's outgoing pair list (indices into it)
 };
 
 // Everything the edge kernel needs for one pair i -> j, built by the pair setup (a1):
@@ -118,6 +125,11 @@ struct StepArgs {
   double* lambda;
   int32_t* flag;                     // bit 0: non-finite loss/gradient
   unsigned int* done;                // completion counter of the pose kernel
+  int32_t n_loss_chunks;             // pose-kernel blocks that sum the per-pair losses
+  const int32_t* loss_chunk_off;     // n_scenes + 1: the scene's chunks (kLossChunk pairs each)
+  const int32_t* loss_chunk_scene;   // n_loss_chunks
+  double* loss_part;                 // n_loss_chunks partial sums of l_p
+  unsigned int* scene_done;          // n_scenes completion counters of the loss chunks
   unsigned int* q_count;             // exact-path sample counter, reset by the pair setup
   int* tile_counter;                 // edge-kernel work counter, reset by the pair setup
   const double* gscale;              // per-scene scale of the gradient (NULL = 1)

@@ -125,6 +125,24 @@ def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
     check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=st)
 
 
+@pytest.mark.parametrize("tail", [1, 2, 3])
+def test_split_last_wave_matches_oracle(ring8, tail):
+    """Work items of the last wave split into items of `tail` pairs (on this small scene the
+    whole tile list is one wave, so every item is split)."""
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, tail_pairs=tail)
+    assert s.info().tail_pairs == tail
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=s.pair_stats())
+    ref = gpu_scene(sc, maps, tail_pairs=0)
+    ref.set_poses(sc.T_init)
+    assert s.info().n_tiles > ref.info().n_tiles
+    l0, g0 = ref.loss_and_grad()
+    assert loss[0] == pytest.approx(l0[0], rel=1e-12) and grad_rel_err(grad, g0) < 1e-10
+
+
 def test_gather_paths_and_schedules_agree(ring8):
     sc, maps = ring8
     res = []
