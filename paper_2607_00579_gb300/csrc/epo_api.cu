@@ -78,6 +78,7 @@ struct epo_scene {
   int32_t n_tiles = 0;
   int tiles_for = -1;   // tile size the current table was built for
   int tiles_tail = -1;  // and its tail split
+  int tiles_grid = -1;  // over the last wave of this many blocks
   int tail = 0;         // pairs per work item of the last wave (0 = not split)
   struct TileTable {
     int tile, tail, grid;
@@ -219,14 +220,16 @@ int resident_blocks(epo_scene* S, int gather, int rpt, int block);
 // of a grid of that many blocks), which are split into items of at most `tail` pairs so
 // that the blocks run out of work at nearly the same time.
 epo_status build_tiles(epo_scene* S, int tile, int tail, int grid) {
-  if (S->tiles_for == tile && S->tiles_tail == tail) return EPO_OK;
+  if (tail == 0) grid = 0;
+  if (S->tiles_for == tile && S->tiles_tail == tail && S->tiles_grid == grid) return EPO_OK;
   S->graph_dirty = true;
   for (const auto& tt : S->tile_tables)
-    if (tt.tile == tile && tt.tail == tail && (tail == 0 || tt.grid == grid)) {
+    if (tt.tile == tile && tt.tail == tail && tt.grid == grid) {
       S->d_tiles = tt.p;
       S->n_tiles = tt.n;
       S->tiles_for = tile;
       S->tiles_tail = tail;
+      S->tiles_grid = grid;
       return EPO_OK;
     }
   std::vector<TileDev> t;
@@ -264,14 +267,17 @@ epo_status build_tiles(epo_scene* S, int tile, int tail, int grid) {
   S->n_tiles = (int32_t)t.size();
   S->tiles_for = tile;
   S->tiles_tail = tail;
+  S->tiles_grid = grid;
   return EPO_OK;
 }
 
-// The work items of the current schedule.
+// Work items of a schedule: block * rpt records each; the last wave is one item per
+// resident block.
 epo_status build_tiles(epo_scene* S, int gather, int rpt, int block, int tail) {
   return build_tiles(S, block * rpt, tail, tail ? resident_blocks(S, gather, rpt, block) : 0);
 }
 
+// The work items of the current schedule.
 epo_status build_tiles(epo_scene* S) { return build_tiles(S, S->gather, S->rpt, S->block, S->tail); }
 
 EdgeArgs edge_args(epo_scene* S) {

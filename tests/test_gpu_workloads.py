@@ -128,6 +128,7 @@ def test_ring32_200_steps_track_oracle(ring32):
     s = gpu_scene(sc, maps, **kw)
     s.set_poses(sc.T_init)
     o = oracle_of(sc, maps)
+    g0 = np.linalg.norm(o.loss_grad(sc.T_init, lam=10.0)["grad"], axis=1).max()
     step = 0
     for c in (50, 100, 150, 200):
         s.step(c - step)
@@ -135,7 +136,7 @@ def test_ring32_200_steps_track_oracle(ring32):
         loss, grad = s.loss_and_grad()
         T = s.get_poses()
         r = o.loss_grad(T, lam=oracle.lambda_at(step))
-        check_against_oracle(loss[0], grad, r, sc.pairs, T, lam=oracle.lambda_at(step))
+        check_against_oracle(loss[0], grad, r, sc.pairs, T, lam=oracle.lambda_at(step), gref=g0)
     Tg = s.get_poses()
     To, sep_r, sep_t, hist = oracle_envelope(o, sc, 200, (50, 100, 150, 200), kw)
     assert rot_err_deg(Tg, To).max() <= 3.0 * max(sep_r, 0.01)
@@ -255,6 +256,7 @@ def test_ring500_bf16_fp16_subset_parity_and_precision_cost(ring500):
     assert grad_rel_err(grad, r["grad"]) <= 1e-2
     # the optimisation: kernel parity along the GPU's trajectory, and the same final accuracy
     # as the oracle on full-precision inputs
+    g0 = np.linalg.norm(o_same.loss_grad(sc.T_init, lam=10.0)["grad"], axis=1).max()
     step = 0
     for c in (50, 100):
         s.step(c - step)
@@ -262,7 +264,7 @@ def test_ring500_bf16_fp16_subset_parity_and_precision_cost(ring500):
         T = s.get_poses()
         loss, grad = s.loss_and_grad()
         check_against_oracle(loss[0], grad, o_same.loss_grad(T, lam=oracle.lambda_at(step)), sc.pairs, T,
-                             lam=oracle.lambda_at(step))
+                             lam=oracle.lambda_at(step), gref=g0)
     To, _, _, _ = o_full.optimize(sc.T_init, sc.fixed, 100, **kw)
     same_accuracy(s.get_poses(), To, sc)
 
