@@ -108,6 +108,12 @@ struct epo_scene {
   int32_t *d_loss_chunk_off = nullptr, *d_loss_chunk_scene = nullptr;
   double* d_loss_part = nullptr;
   unsigned int* d_scene_done = nullptr;
+  int2* d_loss_chunk_pairs = nullptr;
+  int2* d_pair_ij = nullptr;
+  double* d_pair_lw = nullptr;
+  PoseEntry* d_pose_entries = nullptr;
+  int32_t pose_stride = 1;
+  std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
   int64_t device_bytes = 0;
   // stage timing events (options.timing): before setup, after setup, after the edge
@@ -160,6 +166,38 @@ epo_status dalloc(epo_scene* S, T** p, size_t count) {
     if (st_ != EPO_OK) return st_;              \
   } while (0)
 
+// Pair weights in their scene's loss and the per-pose gather entries, from the active pair
+// set (rebuilt whenever it changes).
+epo_status upload_weights(epo_scene* S, cudaStream_t st) {
+  const bool norm_all = S->opt.norm_mode == EPO_NORM_ALL;
+  std::vector<double> lw(S->n_pairs, 0.0);
+  for (int p = 0; p < S->n_pairs; ++p) {
+    const int sc = S->pair_scene[p];
+    const int na = S->scene_active[sc];
+    if (!S->active[p] || na <= 0) continue;
+    double w = 2.0 / na;
+    if (norm_all) {
+      const int64_t n = S->views[S->pair_src[p]].n_rec;
+      w = n > 0 ? w / (double)n : 0.0;
+    }
+    lw[p] = w;
+  }
+  std::vector<PoseEntry> ent((size_t)S->n_views * S->pose_stride, PoseEntry{-1, 0, 0.0});
+  for (int v = 0; v < S->n_views; ++v)
+    for (int k = S->pose_off[v]; k < S->pose_off[v + 1]; ++k) {
+      const int ref = S->pose_ref[k], p = ref >> 1;
+      PoseEntry& e = ent[(size_t)v * S->pose_stride + (k - S->pose_off[v])];
+      if (lw[p] == 0.0) continue;
+      e.p = p;
+      e.scene_role = (S->pair_scene[p] << 1) | (ref & 1);
+      e.w = lw[p];
+    }
+  CK(cudaMemcpyAsync(S->d_pair_lw, lw.data(), lw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(S->d_pose_entries, ent.data(), ent.size() * sizeof(PoseEntry), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  return EPO_OK;
+}
+
 StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   StepArgs a;
   memset(&a, 0, sizeof(a));
@@ -198,6 +236,11 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.loss_chunk_scene = S->d_loss_chunk_scene;
   a.loss_part = S->d_loss_part;
   a.scene_done = S->d_scene_done;
+  a.loss_chunk_pairs = S->d_loss_chunk_pairs;
+  a.pair_ij = S->d_pair_ij;
+  a.pair_lw = S->d_pair_lw;
+  a.pose_entries = S->d_pose_entries;
+  a.pose_stride = S->pose_stride;
   a.gscale = gscale;
   a.lambda0 = S->opt.lambda0;
   a.lambda1 = S->opt.lambda1;
@@ -564,7 +607,10 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     for (int p = 0; p < np; ++p) S->src_pair_ids[fill[S->pair_src[p]]++] = p;
   }
   // per pose: (pair, role) in pair order -> deterministic gather
-  std::vector<int32_t> pose_off(nv + 1, 0), pose_ref(2 * np);
+  std::vector<int32_t>& pose_off = S->pose_off;
+  std::vector<int32_t>& pose_ref = S->pose_ref;
+  pose_off.assign(nv + 1, 0);
+  pose_ref.assign(2 * np, 0);
   for (int v = 0; v < nv; ++v) pose_off[v + 1] = pose_off[v] + pose_pair_cnt[v];
   {
     std::vector<int32_t> fill(pose_off.begin(), pose_off.end() - 1);
@@ -626,10 +672,24 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       chunk_off.push_back(chunk_off.back() + nc);
     }
     S->n_loss_chunks = chunk_off.back();
+    std::vector<int2> chunk_pairs(chunk_scene.size());
+    for (size_t c = 0; c < chunk_scene.size(); ++c) {
+      const int sc = chunk_scene[c];
+      const int first = S->scene_pair_off[sc] + (int)(c - chunk_off[sc]) * kLossChunk;
+      chunk_pairs[c] = make_int2(first, std::min(first + kLossChunk, S->scene_pair_off[sc + 1]));
+    }
     ALLOC(S->d_loss_chunk_off, n_scenes + 1);
     ALLOC(S->d_loss_chunk_scene, chunk_scene.size());
+    ALLOC(S->d_loss_chunk_pairs, chunk_scene.size());
     ALLOC(S->d_loss_part, chunk_scene.size());
     ALLOC(S->d_scene_done, n_scenes);
+    std::vector<int2> pair_ij(np);
+    for (int p = 0; p < np; ++p) pair_ij[p] = make_int2(S->pair_src[p], S->pair_dst[p]);
+    S->pose_stride = 1;
+    for (int v = 0; v < nv; ++v) S->pose_stride = std::max(S->pose_stride, pose_off[v + 1] - pose_off[v]);
+    ALLOC(S->d_pair_ij, np);
+    ALLOC(S->d_pair_lw, np);
+    ALLOC(S->d_pose_entries, (size_t)nv * S->pose_stride);
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
     cudaStream_t st = S->stream;
     if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
@@ -689,6 +749,10 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     CK(cudaMemsetAsync(S->d_done, 0, 4, st));
     CK(cudaMemsetAsync(S->d_scene_done, 0, 4 * (size_t)n_scenes, st));
     CK(cudaMemcpyAsync(S->d_loss_chunk_off, chunk_off.data(), chunk_off.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!chunk_pairs.empty())
+      CK(cudaMemcpyAsync(S->d_loss_chunk_pairs, chunk_pairs.data(), chunk_pairs.size() * sizeof(int2),
+                         cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->d_pair_ij, pair_ij.data(), (size_t)np * sizeof(int2), cudaMemcpyHostToDevice, st));
     if (!chunk_scene.empty())
       CK(cudaMemcpyAsync(S->d_loss_chunk_scene, chunk_scene.data(), chunk_scene.size() * 4, cudaMemcpyHostToDevice,
                          st));
@@ -727,6 +791,33 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     }
     std::vector<unsigned long long> th(S->tex.begin(), S->tex.end());
     CK(cudaMemcpyAsync(S->d_tex, th.data(), nv * 8, cudaMemcpyHostToDevice, st));
+    // the fields of every PairParam that do not change with the poses: the target's
+    // intrinsics, map and the constants of the rounding-error bound (the pair setup writes
+    // the relative pose and its bound each step)
+    {
+      std::vector<PairParam> pp(np);
+      for (int p = 0; p < np; ++p) {
+        PairParam& q = pp[p];
+        memset(&q, 0, sizeof(q));
+        const ViewDev& vj = S->views[S->pair_dst[p]];
+        q.fx = vj.fx; q.fy = vj.fy; q.cx = vj.cx; q.cy = vj.cy;
+        q.fx2 = 2.f * vj.fx;
+        q.fy2 = 2.f * vj.fy;
+        q.hw = 0.5f * (float)(vj.W - 1);
+        q.hh = 0.5f * (float)(vj.H - 1);
+        q.cu = 4.f * kU32 * (float)(vj.W + 1);
+        q.cv = 4.f * kU32 * (float)(vj.H + 1);
+        q.W = vj.W; q.H = vj.H; q.pitch = vj.pitch;
+        q.map_off = vj.map_off;
+        q.tex = th[S->pair_dst[p]];
+      }
+      CK(cudaMemcpyAsync(S->d_pp, pp.data(), (size_t)np * sizeof(PairParam), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    {
+      epo_status ws = upload_weights(S, st);
+      if (ws != EPO_OK) return ws;
+    }
     if (o.timing)
       for (auto& e2 : S->ev) CK(cudaEventCreate(&e2));
     // schedule
@@ -1043,8 +1134,7 @@ epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
   }
   CK(cudaMemcpyAsync(S->d_active, S->active.data(), S->n_pairs, cudaMemcpyHostToDevice, S->stream));
   CK(cudaMemcpyAsync(S->d_scene_active, S->scene_active.data(), S->n_scenes * 4, cudaMemcpyHostToDevice, S->stream));
-  CK(cudaStreamSynchronize(S->stream));
-  return EPO_OK;
+  return upload_weights(S, S->stream);
 }
 
 // Times every schedule of the edge kernel on this scene and keeps the fastest. Launches of

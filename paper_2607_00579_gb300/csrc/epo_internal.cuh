@@ -98,11 +98,22 @@ struct EdgeArgs {
   float eps_z;
 };
 
+// One (pair, role) entry of a pose's gradient gather, laid out at a fixed stride per pose so
+// that the pose kernel reads it without an offset table.  w holds the pair's weight in the
+// scene's loss: 2 / (active pairs of the scene), times 1 / |E_i| under the Eq. 7
+// normaliser; p < 0 marks padding and inactive pairs.
+struct PoseEntry {
+  int32_t p;
+  int32_t scene_role;  // scene << 1 | role (0 = target view j, 1 = source view i)
+  double w;
+};
+
 struct StepArgs {
   int32_t n_views, n_pairs, n_scenes;
   const unsigned long long* tex;     // n_views texture objects (copied into PairParam)
   const int32_t* pair_src;
   const int32_t* pair_dst;
+  const int2* pair_ij;               // (i, j) of every pair
   const int32_t* pair_scene;
   const uint8_t* pair_active;
   const int32_t* scene_pair_off;     // n_scenes + 1 (pairs of a scene are contiguous)
@@ -129,6 +140,10 @@ struct StepArgs {
   const int32_t* loss_chunk_off;     // n_scenes + 1: the scene's chunks (kLossChunk pairs each)
   const int32_t* loss_chunk_scene;   // n_loss_chunks
   double* loss_part;                 // n_loss_chunks partial sums of l_p
+  const int2* loss_chunk_pairs;      // n_loss_chunks: [first, end) pairs of the chunk
+  const double* pair_lw;             // n_pairs: loss weight of the pair (PoseEntry::w), 0 if inactive
+  const PoseEntry* pose_entries;     // n_views x pose_stride
+  int32_t pose_stride;
   unsigned int* scene_done;          // n_scenes completion counters of the loss chunks
   unsigned int* q_count;             // exact-path sample counter, reset by the pair setup
   int* tile_counter;                 // edge-kernel work counter, reset by the pair setup

@@ -35,8 +35,9 @@ __device__ __forceinline__ double lambda_at(const StepArgs& a, int64_t s) {
 }
 
 // 16 lanes per pair (two pairs per warp): lanes 0..8 form one entry of R_ji each, lanes
-// 9..11 one entry of t_ji, lanes 12..15 the target's intrinsics and map; every lane's
-// FP64 chain is a few operations long.
+// 9..11 one entry of t_ji, lane 15 the rounding bound of the FP32 translation; every lane's
+// FP64 chain is a few operations long.  The rest of the PairParam (the target's intrinsics
+// and map) does not change with the poses and is written when the scene is created.
 constexpr int kSetupLanes = 16;
 constexpr int kSetupThreads = 32;  // two pairs per block: the FP64 chains spread over SMs
 
@@ -52,8 +53,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   const int e = lane & 15;
   const int p = gt / kSetupLanes;
   const bool pv = p < a.n_pairs;
-  const int i = pv ? a.pair_src[p] : 0;
-  const int j = pv ? a.pair_dst[p] : 0;
+  const int2 ij = pv ? a.pair_ij[p] : make_int2(0, 0);
+  const int i = ij.x, j = ij.y;
   const double* Ti = a.T + 12 * (size_t)i;
   const double* Tj = a.T + 12 * (size_t)j;
   double val = 0.0;
@@ -82,23 +83,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   if (e < 12) {
     a.pp64[12 * (size_t)p + e] = val;  // R (9) then t (3), as in PairParam
     of[e] = vf;
-  } else if (e == 12) {
-    const ViewDev vj = a.views[j];
-    out->fx = vj.fx; out->fy = vj.fy; out->cx = vj.cx; out->cy = vj.cy;
-    out->fx2 = 2.f * vj.fx;
-    out->fy2 = 2.f * vj.fy;
-  } else if (e == 13) {
-    const ViewDev vj = a.views[j];
-    out->hw = 0.5f * (float)(vj.W - 1);
-    out->hh = 0.5f * (float)(vj.H - 1);
-    out->cu = 4.f * kU32 * (float)(vj.W + 1);
-    out->cv = 4.f * kU32 * (float)(vj.H + 1);
-  } else if (e == 14) {
-    const ViewDev vj = a.views[j];
-    out->W = vj.W; out->H = vj.H; out->pitch = vj.pitch;
-    out->map_off = vj.map_off;
-    out->tex = a.tex ? a.tex[j] : 0ull;
-  } else {
+  } else if (e == 15) {
     out->Et = 4.f * kU32 * (fabsf(t0) + fabsf(t1) + fabsf(t2));
   }
   if (e < kAcc) {
@@ -141,22 +126,41 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     const int e = lane & 15;
     const int v = blockIdx.x * kPosesPerBlock + (threadIdx.x >> 4);
     const bool vv = v < a.n_views && with_grad > 0;
+    // the optimiser state and the old pose do not depend on the gradient: their loads are
+    // issued first, so that they overlap the gather below
+    double m_old = 0.0, v_old = 0.0, Tc0 = 0.0, Tc1 = 0.0, Tc2 = 0.0, bp0 = 0.0, bp1 = 0.0;
+    if (with_grad == 2 && vv) {
+      if (e < 6) {
+        m_old = a.m[6 * (size_t)v + e];
+        v_old = a.v[6 * (size_t)v + e];
+      }
+      if (e < 12) {
+        const double* T = a.T_store + 12 * (size_t)v;
+        Tc0 = T[e & 3];
+        Tc1 = T[4 + (e & 3)];
+        Tc2 = T[8 + (e & 3)];
+      }
+      bp0 = a.bpow[0];
+      bp1 = a.bpow[1];
+    }
     double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (vv) {
-      for (int k = a.pose_pair_off[v] + e; k < a.pose_pair_off[v + 1]; k += 16) {
-        const int ref = a.pose_pair_ref[k];
-        const int p = ref >> 1;
-        if (!a.pair_active[p]) continue;
+      const PoseEntry* ent = a.pose_entries + (size_t)v * a.pose_stride;
+      for (int k = e; k < a.pose_stride; k += 16) {
+        const PoseEntry en = ent[k];
+        if (en.p < 0) continue;
+        const int p = en.p;
         const double* acc = a.pair_acc + (size_t)kAcc * p;
-        const int i = a.pair_src[p];
-        const double denom = a.norm_all ? (double)a.views[i].n_rec : acc[1];
-        const int s = a.pair_scene[p];
-        const int na = a.scene_active_pairs[s];
-        if (!(denom > 0.0) || na <= 0) continue;
-        const double c = (a.gscale ? a.gscale[s] : 1.0) * __drcp_rn((double)na * 0.5 * denom);
+        double c = en.w;  // the pair's weight in its scene's loss
+        if (!a.norm_all) {
+          const double n = acc[1];  // Algorithm 3: the pair's mean runs over its valid samples
+          if (!(n > 0.0)) continue;
+          c *= __drcp_rn(n);
+        }
+        if (a.gscale) c *= a.gscale[en.scene_role >> 1];
         const double ga0 = c * acc[2], ga1 = c * acc[3], ga2 = c * acc[4];
         const double gb0 = c * acc[5], gb1 = c * acc[6], gb2 = c * acc[7];
-        if ((ref & 1) == 0) {  // target view j: the 6-vector as is
+        if ((en.scene_role & 1) == 0) {  // target view j: the 6-vector as is
           g[0] += ga0; g[1] += ga1; g[2] += ga2;
           g[3] += gb0; g[4] += gb1; g[5] += gb2;
         } else {
@@ -193,13 +197,13 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       double xi = 0.0;
       if (!skip && e < 6) {
         const size_t o = 6 * (size_t)v + e;
-        const double m = a.beta1 * a.m[o] + (1.0 - a.beta1) * G;
-        const double vm = a.beta2 * a.v[o] + (1.0 - a.beta2) * G * G;
+        const double m = a.beta1 * m_old + (1.0 - a.beta1) * G;
+        const double vm = a.beta2 * v_old + (1.0 - a.beta2) * G * G;
         a.m[o] = m;
         a.v[o] = vm;
         // the step ratio m^ / (sqrt(v^) + eps) needs only single precision
-        const float mh = (float)m / (1.f - (float)a.bpow[0]);
-        const float vh = (float)vm / (1.f - (float)a.bpow[1]);
+        const float mh = (float)m / (1.f - (float)bp0);
+        const float vh = (float)vm / (1.f - (float)bp1);
         const float lr = (float)(e < 3 ? a.lr_trans : a.lr_rot);
         xi = -(double)(lr * mh / (sqrtf(vh) + (float)a.adam_eps));  // the update is Exp(-Delta)
       }
@@ -247,10 +251,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       const double E2 = __shfl_sync(0xffffffffu, Erc, rb + 2);
       const double E3 = __shfl_sync(0xffffffffu, Erc, rb + 3);
       double Tnew = 0.0;
-      if (!skip && e < 12) {
-        const double* T = a.T_store + 12 * (size_t)v;
-        Tnew = fma(E0, T[c], fma(E1, T[4 + c], fma(E2, T[8 + c], c == 3 ? E3 : 0.0)));
-      }
+      if (!skip && e < 12) Tnew = fma(E0, Tc0, fma(E1, Tc1, fma(E2, Tc2, c == 3 ? E3 : 0.0)));
       __syncwarp();  // every lane has read the old pose before any lane writes it
       if (!skip && e < 12) a.T_store[12 * (size_t)v + e] = Tnew;
     }
@@ -260,12 +261,19 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     // the scene's partial sums in a fixed order, so the loss does not depend on timing
     const int c = blockIdx.x - n_pose_blocks;
     const int s = a.loss_chunk_scene[c];
-    const int p = a.scene_pair_off[s] + (c - a.loss_chunk_off[s]) * kLossChunk + (int)threadIdx.x;
+    const int2 range = a.loss_chunk_pairs[c];
+    const int p = range.x + (int)threadIdx.x;
     double acc = 0.0;
-    if (p < a.scene_pair_off[s + 1] && a.pair_active[p]) {
-      const double* pa = a.pair_acc + (size_t)kAcc * p;
-      const double denom = a.norm_all ? (double)a.views[a.pair_src[p]].n_rec : pa[1];
-      if (denom > 0.0) acc = pa[0] * __drcp_rn(denom);
+    if (p < range.y) {
+      const double w = a.pair_lw[p];  // 0 for an inactive pair
+      if (w != 0.0) {
+        const double* pa = a.pair_acc + (size_t)kAcc * p;
+        if (a.norm_all) {
+          acc = w * pa[0];
+        } else if (pa[1] > 0.0) {
+          acc = w * pa[0] * __drcp_rn(pa[1]);
+        }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -284,8 +292,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (threadIdx.x == 0) {
-        const int na = a.scene_active_pairs[s];
-        const double L = na > 0 ? (2.0 / na) * t : 0.0;
+        const double L = t;  // the weights carry the 2 / (active pairs) factor
         a.loss[s] = L;
         if (!isfinite(L)) atomicOr(a.flag, 1);
         a.scene_done[s] = 0u;
