@@ -261,14 +261,37 @@ def oracle_sample(wl, budget_s, seed=0):
 
 
 def cpu_baseline(wl, budget_s=12.0):
+    """The oracle on all host cores (the reported value), and on one thread for reference."""
+    import oracle
+    cores = oracle.set_threads(oracle_threads())
     osc, T, fx, ev, n_pairs = oracle_sample(wl, budget_s / 4)
     dt1, _ = time_oracle_steps(osc, T, fx, 1)
-    n = max(1, int(budget_s / max(dt1, 1e-3)))
+    n = max(1, int(0.75 * budget_s / max(dt1, 1e-3)))
     dt, _ = time_oracle_steps(osc, T, fx, n)
-    return {"value": ev * n / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+    oracle.set_threads(1)
+    dts, _ = time_oracle_steps(osc, T, fx, 1)
+    oracle.set_threads(cores)
+    return {"value": ev * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": ev / dts,
             "sample": f"{n} oracle optimisation steps (FP64, OpenMP over pairs) on {n_pairs} of the "
                       f"{wl.scenes[0].n_pairs} pairs of the {'first scene of the ' if len(wl.scenes) > 1 else ''}"
-                      f"{wl.name} workload ({ev} evals per step), {ev * n} evals in {dt:.2f} s"}
+                      f"{wl.name} workload ({ev} evals per step), {ev * n} evals in {dt:.2f} s; "
+                      f"single_thread_value: one such step on 1 thread in {dts:.2f} s"}
+
+
+def job_throughput(units, ms, device="cpu"):
+    """Whole-job rate over the ranks of the default process group (or this process alone):
+    the units all ranks processed divided by the slowest rank's time."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return units / (ms * 1e-3), ms
+    import torch.distributed as dist
+    t = torch.tensor([float(units), float(ms)], dtype=torch.float64, device=device)
+    u = t[:1].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    m = t[1:].clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()) / (float(m.item()) * 1e-3), float(m.item())
 
 
 def run_reference(args):
@@ -402,13 +425,7 @@ def run_ours(args):
         stages.append(epo._binding.epo_stage_times(st_.handle))
     st_.check()
     clk = clocks.stop()
-    tot_ms = float(np.sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * evals * args.steps / (tot_ms * 1e-3)
+    value, tot_ms = job_throughput(evals * args.steps, float(np.sum(step_ms)), "cuda")
 
     # end to end through the public API with host buffers: pinned poses in, step, poses + loss out
     T_host = torch.from_numpy(T_init.copy()).pin_memory()

@@ -83,6 +83,8 @@ def _load():
         lib.oracle_lambda.argtypes = [P, ctypes.c_int64]
         lib.oracle_lambda.restype = ctypes.c_double
         lib.oracle_optimize.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P]
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -210,6 +212,11 @@ class OracleScene:
         if rc:
             raise ValueError(f"oracle_optimize failed ({rc})")
         return T, m, v, hist[:n_steps]
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the OpenMP loops (n > 0 sets them); returns the count in effect."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def lambda_at(step: int, lambda0=10.0, lambda1=6.0, lambda_steps=1000) -> float:

@@ -27,6 +27,9 @@
  * Precision: every value is double; inputs that the GPU stores in reduced
  * precision are passed here already rounded and widened.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -78,6 +81,18 @@ static void edt_1d(const double* f, int n, double* d, int* v, double* z) {
 
 /* dist[y*W + x] = Euclidean distance from pixel (x, y) to the nearest edge
  * pixel; a view without edges gets W + H everywhere. */
+/* Number of OpenMP threads the loss and gradient use (n > 0 sets it); returns the count in
+ * effect.  Timing aid for the CPU baseline: one thread against all cores. */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int oracle_edt(const uint8_t* edge, int W, int H, double* dist) {
   if (W < 1 || H < 1) return ORACLE_EINVAL;
   int any = 0;

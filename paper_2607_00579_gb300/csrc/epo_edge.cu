@@ -116,10 +116,17 @@ struct AmbEntry {
 };
 constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
 
-// The exact path: lift, transform and project in FP64, take the validity, cell and clamp
-// decisions in FP64 (so the branch is the one an FP64 evaluation takes); the value and the
-// slope terms are smooth given those decisions and are formed in FP32.  Adds straight to
-// the pair's FP64 accumulators.
+// The exact path.  The lift and the transform run in FP64; every decision (in front, in
+// bounds, bilinear cell, clamp) is then the one the FP64 evaluation of the definition takes,
+// with as little FP64 arithmetic as that needs (on this GPU FP64 runs at 1/64 of FP32):
+//   * with s_u = fx Y1 + cx Y3 = Y3 u' (Y3 > 0), u' >= k  <=>  s_u - k Y3 >= 0, so the border
+//     and the cell are signs of single FMAs: no FP64 division;
+//   * the cell index starts from an FP32 estimate of u' (relative error < 3e-7, so within
+//     one cell) and is corrected by those signs;
+//   * the bilinear value and slopes are formed in FP32 from the cell fractions; the clamp
+//     decision d <= lambda takes the FP32 value unless it lies within its error bound of
+//     lambda, in which case the fractions and d are formed again in FP64.
+// Adds straight to the pair's FP64 accumulators.
 template <int MODE, int MAP>
 __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, float lamf) {
   const int p = en.p;
@@ -135,19 +142,39 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, fl
 #pragma unroll
   for (int r = 0; r < 3; ++r) Y[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + R[9 + r];
   if (!(Y[2] > (double)a.eps_z)) return;
-  const double iz = __drcp_rn(Y[2]);
-  const double up = Kj[0] * Y[0] * iz + Kj[2];
-  const double vp = Kj[1] * Y[1] * iz + Kj[3];
-  if (!(up >= 0.0 && up <= (double)(P.W - 1) && vp >= 0.0 && vp <= (double)(P.H - 1))) return;
-  const int x0 = min((int)floor(up), P.W - 2);
-  const int y0 = min((int)floor(vp), P.H - 2);
-  const double ca = up - (double)x0, cb = vp - (double)y0;
+  const double su = fma(Kj[0], Y[0], Kj[2] * Y[2]);  // Y3 u'
+  const double sv = fma(Kj[1], Y[1], Kj[3] * Y[2]);  // Y3 v'
+  if (!(su >= 0.0 && fma(-(double)(P.W - 1), Y[2], su) <= 0.0 && sv >= 0.0 &&
+        fma(-(double)(P.H - 1), Y[2], sv) <= 0.0))
+    return;
+  const float rz = rcp_approx((float)Y[2]);
+  int x0 = __float2int_rd((float)su * rz), y0 = __float2int_rd((float)sv * rz);
+  if (fma(-(double)x0, Y[2], su) < 0.0) --x0;
+  else if (fma(-(double)(x0 + 1), Y[2], su) >= 0.0) ++x0;
+  if (fma(-(double)y0, Y[2], sv) < 0.0) --y0;
+  else if (fma(-(double)(y0 + 1), Y[2], sv) >= 0.0) ++y0;
+  x0 = min(x0, P.W - 2);  // the last cell is clamped (u' = W - 1 is in bounds)
+  y0 = min(y0, P.H - 2);
+  const double sa = fma(-(double)x0, Y[2], su), sb = fma(-(double)y0, Y[2], sv);  // Y3 (u' - x0), Y3 (v' - y0)
   float f00, f01, f10, f11;
   taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, x0, y0, f00, f01, f10, f11);
-  const double d = (1.0 - ca) * (1.0 - cb) * f00 + ca * (1.0 - cb) * f01 + (1.0 - ca) * cb * f10 + ca * cb * f11;
-  const bool pass = d <= lam;  // clamp decision in FP64
+  const float caf = (float)sa * rz, cbf = (float)sb * rz;  // relative error < 3e-7
+  const float top = fmaf(caf, f01 - f00, f00), bot = fmaf(caf, f11 - f10, f10);
+  float df = fmaf(cbf, bot - top, top);
+  const float ddu = fmaf(cbf, (f11 - f10) - (f01 - f00), f01 - f00);
+  const float ddv = bot - top;
+  bool pass;
+  const float tcl = 2.f * (6e-7f * (fabsf(ddu) + fabsf(ddv)) + 8.f * kU32 * (fabsf(df) + 1.f));
+  if (fabsf(df - lamf) > tcl) {
+    pass = df <= lamf;
+  } else {  // near the clamp: decide on the FP64 value
+    const double iz = 1.0 / Y[2];
+    const double ca = sa * iz, cb = sb * iz;
+    const double d = (1.0 - ca) * (1.0 - cb) * f00 + ca * (1.0 - cb) * f01 + (1.0 - ca) * cb * f10 + ca * cb * f11;
+    pass = d <= lam;
+    df = (float)d;
+  }
   const float delta = a.delta;
-  const float df = (float)d, caf = (float)ca, cbf = (float)cb;
   const float dh = pass ? df : lamf;
   const float adh = fabsf(dh);
   const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
@@ -159,13 +186,10 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, fl
   if constexpr (MODE != MODE_FWD) {
     const float drho = pass ? (fabsf(df) <= delta ? df : copysignf(delta, df)) : 0.f;
     if (drho != 0.f) {
-      const float ddu = (1.f - cbf) * (f01 - f00) + cbf * (f11 - f10);
-      const float ddv = (1.f - caf) * (f10 - f00) + caf * (f11 - f01);
       const float y0f = (float)Y[0], y1f = (float)Y[1], y2f = (float)Y[2];
-      const float izf = (float)iz;
-      const float gx = drho * ddu * P.fx * izf;
-      const float gy = drho * ddv * P.fy * izf;
-      const float gz = -(gx * y0f + gy * y1f) * izf;
+      const float gx = drho * ddu * P.fx * rz;
+      const float gy = drho * ddv * P.fy * rz;
+      const float gz = -(gx * y0f + gy * y1f) * rz;
       atomicAdd(acc + 2, (double)gx);
       atomicAdd(acc + 3, (double)gy);
       atomicAdd(acc + 4, (double)gz);
