@@ -83,6 +83,7 @@ def _load():
         lib.oracle_lambda.argtypes = [P, ctypes.c_int64]
         lib.oracle_lambda.restype = ctypes.c_double
         lib.oracle_optimize.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P]
+        lib.oracle_loss_grad_full.argtypes = [P] * 11
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -195,6 +196,28 @@ class OracleScene:
         return dict(loss=float(loss[0]), grad=grad, pair_stats=st[:self.n_pairs],
                     pair_near=near[:self.n_pairs], pair_loss=pl[:self.n_pairs], pair_abs=ab[:self.n_pairs],
                     pair_maxterm=mt[:self.n_pairs])
+
+    def loss_grad_full(self, T: np.ndarray, gamma: np.ndarray, alpha: np.ndarray, beta: np.ndarray, lam: float,
+                       delta: float = 1.0, eps_z: float = 1e-6, norm_mode: int = NORM_VALID):
+        """Objective with focal scales gamma (per view, f = f0 (1 + gamma)) and per-record depth
+        parameters (z = z0 alpha + beta).  Returns dict(loss, grad (n,6), grad_gamma (n,),
+        grad_alpha (n_rec,), grad_beta (n_rec,))."""
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12)
+        g = np.ascontiguousarray(gamma, dtype=np.float64).reshape(self.n_views)
+        n_rec = self.rec.shape[0]
+        a = np.ascontiguousarray(alpha, dtype=np.float64).reshape(n_rec)
+        b = np.ascontiguousarray(beta, dtype=np.float64).reshape(n_rec)
+        prm = _Params(lam, delta, eps_z, norm_mode, 1e-9)
+        loss = np.zeros(1)
+        grad = np.zeros((self.n_views, 6))
+        gg = np.zeros(self.n_views)
+        ga = np.zeros(max(n_rec, 1))
+        gb = np.zeros(max(n_rec, 1))
+        rc = _load().oracle_loss_grad_full(ctypes.byref(self._s), _p(T), _p(g), _p(a), _p(b), ctypes.byref(prm),
+                                           _p(loss), _p(grad), _p(gg), _p(ga), _p(gb))
+        if rc:
+            raise ValueError(f"oracle_loss_grad_full failed ({rc})")
+        return dict(loss=float(loss[0]), grad=grad, grad_gamma=gg, grad_alpha=ga[:n_rec], grad_beta=gb[:n_rec])
 
     def optimize(self, T: np.ndarray, fixed: np.ndarray, n_steps: int, *, lambda0=10.0, lambda1=6.0,
                  lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID, lr_rot=1e-3,

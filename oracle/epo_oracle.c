@@ -368,6 +368,125 @@ int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params
 }
 
 /* ------------------------------------------------------------------ */
+/* Camera and depth refinement (Section 3, Camera Refinement and Depth  */
+/* Refinement, Eqs. 4-5): f_i = f_i^0 (1 + gamma_i) scales both focal    */
+/* lengths of view i; each edge pixel's depth is Z^0 alpha + beta.       */
+/* ------------------------------------------------------------------ */
+/*
+ * Objective (Eqs. 6-8) at poses T, focal scales gamma (n_views) and per-record depth
+ * parameters alpha, beta (n_rec), and its gradient with respect to all of them:
+ *   grad (n_views x 6, left perturbation as in oracle_loss_grad), grad_gamma (n_views),
+ *   grad_alpha, grad_beta (n_rec).  Any gradient pointer may be NULL.
+ * Two plain passes: the first sums rho and counts the valid samples of every pair (the
+ * pair means' denominators), the second differentiates every sample with its pair's
+ * weight (2/P) / denom and adds it to the parameters it depends on, pair by pair in order.
+ * For a sample of record r (view i) in pair i -> j, with X_c its camera-i lift, Y its
+ * camera-j position and gY = dRho/dY:
+ *   h = R_i R_j^T gY = dRho/dX_c;
+ *   dRho/dz_r = h . X_c / z_r (X_c is linear in z), so dRho/dalpha_r = dRho/dz_r Z^0_r and
+ *   dRho/dbeta_r = dRho/dz_r;
+ *   dRho/dgamma_i = -(h_0 X_c0 + h_1 X_c1) / (1 + gamma_i) (X_c0, X_c1 scale as 1 / f_i);
+ *   dRho/dgamma_j = drho (dd/du' (u' - c_x) + dd/dv' (v' - c_y)) / (1 + gamma_j)
+ *   (u' - c_x = f_j Y_0 / Y_2 scales as f_j).
+ */
+int oracle_loss_grad_full(const oracle_scene* S0, const double* T, const double* gamma,
+                          const double* alpha, const double* beta, const oracle_params* prm,
+                          double* loss, double* grad, double* grad_gamma, double* grad_alpha,
+                          double* grad_beta) {
+  if (!S0 || !T || !gamma || !alpha || !beta || !prm || !loss) return ORACLE_EINVAL;
+  int n = S0->n_views, P = S0->n_pairs;
+  int64_t n_rec = S0->rec_off[n];
+  /* the refined intrinsics and depths, then the objective of oracle_loss_grad on them */
+  double* K = (double*)malloc(sizeof(double) * 4 * (n > 0 ? n : 1));
+  double* rec = (double*)malloc(sizeof(double) * 3 * (n_rec > 0 ? n_rec : 1));
+  double* gz = (double*)calloc((size_t)(n_rec > 0 ? n_rec : 1), sizeof(double));
+  double* st = (double*)malloc(sizeof(double) * 8 * (P > 0 ? P : 1));
+  if (!K || !rec || !gz || !st) {
+    free(K); free(rec); free(gz); free(st);
+    return ORACLE_ENOMEM;
+  }
+  for (int v = 0; v < n; ++v) {
+    K[4 * v + 0] = S0->K[4 * v + 0] * (1.0 + gamma[v]);
+    K[4 * v + 1] = S0->K[4 * v + 1] * (1.0 + gamma[v]);
+    K[4 * v + 2] = S0->K[4 * v + 2];
+    K[4 * v + 3] = S0->K[4 * v + 3];
+  }
+  for (int64_t r = 0; r < n_rec; ++r) {
+    rec[3 * r + 0] = S0->rec[3 * r + 0];
+    rec[3 * r + 1] = S0->rec[3 * r + 1];
+    rec[3 * r + 2] = S0->rec[3 * r + 2] * alpha[r] + beta[r];
+  }
+  oracle_scene S = *S0;
+  S.K = K;
+  S.rec = rec;
+  int rc = oracle_loss_grad(&S, T, prm, loss, grad, st, NULL, NULL, NULL, NULL);
+  if (rc != ORACLE_OK) {
+    free(K); free(rec); free(gz); free(st);
+    return rc;
+  }
+  if (grad_gamma)
+    for (int v = 0; v < n; ++v) grad_gamma[v] = 0.0;
+  /* second pass: the gradients with respect to gamma and the depths */
+  for (int p = 0; p < P; ++p) {
+    int i = S.pairs[2 * p], j = S.pairs[2 * p + 1];
+    double denom = prm->norm_mode == 1 ? (double)(S.rec_off[i + 1] - S.rec_off[i]) : st[8 * p + 1];
+    if (!(denom > 0)) continue;
+    double c = (2.0 / P) / denom;
+    const double* Ti = T + 12 * i;
+    const double* Tj = T + 12 * j;
+    const double* Ki = K + 4 * i;
+    const double* Kj = K + 4 * j;
+    int Wj = S.W[j], Hj = S.H[j];
+    const double* map = S.map + S.map_off[j];
+    double fx = Kj[0], fy = Kj[1], cx = Kj[2], cy = Kj[3];
+    for (int64_t r = S.rec_off[i]; r < S.rec_off[i + 1]; ++r) {
+      double Xc[3], Xw[3], Y[3];
+      unproject(Ki, Ti, rec + 3 * r, Xc, Xw);
+      mat3_vec(Tj, Xw, Y);
+      if (!(Y[2] > prm->eps_z)) continue;
+      double up = fx * Y[0] / Y[2] + cx;
+      double vp = fy * Y[1] / Y[2] + cy;
+      if (!(up >= 0.0 && up <= Wj - 1 && vp >= 0.0 && vp <= Hj - 1)) continue;
+      int x0 = (int)floor(up);
+      if (x0 > Wj - 2) x0 = Wj - 2;
+      int y0 = (int)floor(vp);
+      if (y0 > Hj - 2) y0 = Hj - 2;
+      double a = up - x0, b = vp - y0;
+      double m00 = map[(int64_t)y0 * Wj + x0];
+      double m01 = map[(int64_t)y0 * Wj + x0 + 1];
+      double m10 = map[(int64_t)(y0 + 1) * Wj + x0];
+      double m11 = map[(int64_t)(y0 + 1) * Wj + x0 + 1];
+      double d = (1 - a) * (1 - b) * m00 + a * (1 - b) * m01 + (1 - a) * b * m10 + a * b * m11;
+      double dd_du = (1 - b) * (m01 - m00) + b * (m11 - m10);
+      double dd_dv = (1 - a) * (m10 - m00) + a * (m11 - m01);
+      double rho, drho;
+      oracle_robust(d, prm->lambda, prm->delta, &rho, &drho);
+      double z = Y[2];
+      double gY[3];
+      gY[0] = drho * dd_du * fx / z;
+      gY[1] = drho * dd_dv * fy / z;
+      gY[2] = -drho * (dd_du * fx * Y[0] + dd_dv * fy * Y[1]) / (z * z);
+      double w[3], h[3];
+      for (int c2 = 0; c2 < 3; ++c2) w[c2] = Tj[c2] * gY[0] + Tj[4 + c2] * gY[1] + Tj[8 + c2] * gY[2];
+      for (int r2 = 0; r2 < 3; ++r2) h[r2] = Ti[4 * r2] * w[0] + Ti[4 * r2 + 1] * w[1] + Ti[4 * r2 + 2] * w[2];
+      /* X_c = z (x~, y~, 1) with x~ = (u - c_x) / f_x: dX_c/dz = (x~, y~, 1) */
+      const double xt = (rec[3 * r + 0] - Ki[2]) / Ki[0], yt = (rec[3 * r + 1] - Ki[3]) / Ki[1];
+      gz[r] += c * (h[0] * xt + h[1] * yt + h[2]);
+      if (grad_gamma) {
+        grad_gamma[i] += c * -(h[0] * Xc[0] + h[1] * Xc[1]) / (1.0 + gamma[i]);
+        grad_gamma[j] += c * drho * (dd_du * (up - cx) + dd_dv * (vp - cy)) / (1.0 + gamma[j]);
+      }
+    }
+  }
+  for (int64_t r = 0; r < n_rec; ++r) {
+    if (grad_alpha) grad_alpha[r] = gz[r] * S0->rec[3 * r + 2];
+    if (grad_beta) grad_beta[r] = gz[r];
+  }
+  free(K); free(rec); free(gz); free(st);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* SE(3): exponential, logarithm, left Jacobian (textbook Lie algebra;  */
 /* xi = (upsilon, omega), translation first).                           */
 /* ------------------------------------------------------------------ */
