@@ -112,6 +112,11 @@ typedef struct {
                                 n > 0 = split into items of at most n pairs, so that the
                                 blocks finish together; -1 = default (autotuned when
                                 autotune is on, else 0) */
+  int32_t refine;            /* 1: the scene also carries the focal and depth refinement of
+                                Section 3 (Eq. 4: f_i = f_i^0 (1 + gamma_i) for both focal
+                                lengths of view i; Eq. 5: every edge pixel's depth is
+                                Z^0 alpha + beta), set by epo_set_refinement and used by every
+                                evaluation and step; two records per thread */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -231,6 +236,26 @@ epo_status epo_kernel_time(epo_scene_t scene, float* ms);
  * ambiguous samples), pose kernel (loss, gradient gather, update).  ms: 3
  * floats.  Needs options.timing = 1.  Synchronises. */
 epo_status epo_stage_times(epo_scene_t scene, float* ms);
+
+/* Focal scales and per-pixel depth parameters of a scene created with
+ * options.refine = 1 (Section 3, Camera Refinement and Depth Refinement,
+ * Eqs. 4-5).  gamma: n_views doubles (> -1), the focal lengths of view v are
+ * f^0 (1 + gamma_v); alpha, beta: one float each per kept record (the records
+ * of epo_scene_info.n_records, in input order without the dropped ones), the
+ * record's depth is z^0 alpha + beta.  Host arrays, copied; NULL = the
+ * identity (0, 1, 0).  Synchronises.  EPO_ERR_INVALID_ARG on a scene without
+ * refinement or non-finite values. */
+epo_status epo_set_refinement(epo_scene_t scene, const double* gamma, const float* alpha, const float* beta);
+
+/* The objective at the current poses and refinement and its gradient with
+ * respect to all of them: loss (n_scenes), grad (n_views x 6, left
+ * perturbation), grad_gamma (n_views), grad_alpha and grad_beta (n_records,
+ * dL/dalpha = dL/dz z^0, dL/dbeta = dL/dz).  Two passes (Algorithm 2's
+ * forward and analytic backward): the forward counts every pair's valid
+ * samples, which weight the per-record depth derivatives of the adjoint.
+ * Host outputs; any gradient may be NULL.  Synchronises. */
+epo_status epo_refine_loss_and_grad(epo_scene_t scene, double* loss, double* grad, double* grad_gamma,
+                                    float* grad_alpha, float* grad_beta);
 
 /* Evaluate only a subset of the pairs from now on (the stochastic viewgraph
  * sub-sampling of Algorithm 3 / Appendix A.3; the draw is the caller's).

@@ -38,7 +38,7 @@ EXPORTED = [
     "epo_loss_and_grad_dev", "epo_pair_stats", "epo_forward_dev", "epo_backward_dev", "epo_step",
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
-    "epo_loss_and_grad_noalloc", "epo_gather_probe",
+    "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
 ]
 
 
@@ -69,7 +69,8 @@ class epo_options(ctypes.Structure):
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
                 ("autotune", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32), ("tail_pairs", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32), ("tail_pairs", ctypes.c_int32),
+                ("refine", ctypes.c_int32)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -272,6 +273,27 @@ def epo_distance_field(edges_dev, W: int, H: int, map_dev, stream: int = 0):
 
 def epo_round_bf16(src_dev, dst_dev, n: int, stream: int = 0):
     check(load().epo_round_bf16(_ptr(src_dev), _ptr(dst_dev), ctypes.c_int64(n), ctypes.c_void_p(stream)))
+
+
+def epo_set_refinement(scene, gamma=None, alpha=None, beta=None):
+    import numpy as np
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float32)
+    b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
+    _call("epo_set_refinement", scene, _ptr(g), _ptr(a), _ptr(b))
+
+
+def epo_refine_loss_and_grad(scene, n_scenes: int, n_views: int, n_records: int):
+    """Returns (loss (n_scenes,), grad (n_views, 6), grad_gamma (n_views,), grad_alpha, grad_beta
+    (n_records,) float32)."""
+    import numpy as np
+    loss = np.zeros(n_scenes)
+    grad = np.zeros((n_views, 6))
+    gg = np.zeros(n_views)
+    ga = np.zeros(max(n_records, 1), dtype=np.float32)
+    gb = np.zeros(max(n_records, 1), dtype=np.float32)
+    _call("epo_refine_loss_and_grad", scene, _ptr(loss), _ptr(grad), _ptr(gg), _ptr(ga), _ptr(gb))
+    return loss, grad, gg, ga[:n_records], gb[:n_records]
 
 
 def epo_gather_probe(n_maps: int, W: int, H: int, map_dtype: int, gather: int, pattern: int, samples: int,

@@ -112,6 +112,10 @@ struct epo_scene {
   int2* d_pair_ij = nullptr;
   double* d_pair_lw = nullptr;
   PoseEntry* d_pose_entries = nullptr;
+  // focal and depth refinement (options.refine)
+  int refine = 0;
+  double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
+  float *d_alpha = nullptr, *d_beta = nullptr, *d_grad_z = nullptr, *d_grad_alpha = nullptr, *d_grad_beta = nullptr;
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
@@ -241,6 +245,12 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.pair_lw = S->d_pair_lw;
   a.pose_entries = S->d_pose_entries;
   a.pose_stride = S->pose_stride;
+  a.refine = S->refine;
+  a.gamma = S->d_gamma;
+  a.K64 = S->d_K64;
+  a.K64r = S->d_K64r;
+  a.pair_facc = S->d_pair_facc;
+  a.grad_gamma = S->d_grad_gamma;
   a.gscale = gscale;
   a.lambda0 = S->opt.lambda0;
   a.lambda1 = S->opt.lambda1;
@@ -348,6 +358,16 @@ EdgeArgs edge_args(epo_scene* S) {
   a.lambda = S->d_lambda;
   a.delta = (float)S->opt.huber_delta;
   a.eps_z = (float)S->opt.eps_z;
+  if (S->refine) {
+    a.K64 = S->d_K64r;  // the lift and the exact path use the refined intrinsics
+    a.gamma = S->d_gamma;
+    a.alpha = S->d_alpha;
+    a.beta = S->d_beta;
+    a.pair_facc = S->d_pair_facc;
+    a.grad_z = S->d_grad_z;
+  }
+  a.pair_lw = S->d_pair_lw;
+  a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
   return a;
 }
 
@@ -356,8 +376,8 @@ EdgeArgs edge_args(epo_scene* S) {
 int resident_blocks(epo_scene* S, int gather, int rpt, int block) {
   if (S->opt.grid_blocks > 0) return S->opt.grid_blocks;
   int per_sm = 0;
-  const void* k = edge_kernel_ptr(MODE_FUSED, S->rec_dtype, S->map_dtype, gather, rpt);
-  const size_t smem = edge_smem_bytes(rpt, block, S->max_pairs);
+  const void* k = edge_kernel_ptr(MODE_FUSED, S->refine, S->rec_dtype, S->map_dtype, gather, rpt);
+  const size_t smem = edge_smem_bytes(rpt, block, S->max_pairs, S->refine);
   if (smem > 48 * 1024 && k) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess || per_sm < 1)
     per_sm = std::max(1, 1024 / block);
@@ -372,7 +392,7 @@ int grid_for(epo_scene* S, int gather, int rpt, int block) {
 constexpr size_t kMaxSmem = 227 * 1024;
 
 bool schedule_fits(epo_scene* S, int rpt, int block) {
-  return edge_smem_bytes(rpt, block, S->max_pairs) <= kMaxSmem;
+  return (!S->refine || rpt == 2) && edge_smem_bytes(rpt, block, S->max_pairs, S->refine) <= kMaxSmem;
 }
 
 // Record stage event k on stream s (inside a capture it becomes an event-record node).
@@ -399,7 +419,7 @@ epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, int 
   if (st != EPO_OK) return st;
   EdgeArgs ea = edge_args(S);
   int grid = grid_for(S, gather, rpt, block);
-  CK(launch_edge(ea, mode, S->rec_dtype, S->map_dtype, gather, rpt, block, grid, s));
+  CK(launch_edge(ea, mode, S->refine, S->rec_dtype, S->map_dtype, gather, rpt, block, grid, s));
   MARK(2, s);
   return EPO_OK;
 }
@@ -408,6 +428,7 @@ epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, int 
 epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval) {
   StepArgs a = step_args(S, T_eval, nullptr);
   MARK(0, s);
+  if (S->refine) CK(launch_refine_intrinsics(a, s));
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
   epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
@@ -422,6 +443,7 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   StepArgs a = step_args(S, S->d_T, nullptr);
   MARK(0, s);
+  if (S->refine) CK(launch_refine_intrinsics(a, s));
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
   epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
@@ -479,6 +501,10 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
   if (o.tail_pairs < -1) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs must be -1, 0 or positive");
+  if (o.refine != 0 && o.refine != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "refine must be 0 or 1");
+  if (o.refine && o.records_per_thread != 0 && o.records_per_thread != 2)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "refine scenes run two records per thread");
+  S->refine = o.refine;
   S->stream = (cudaStream_t)cuda_stream;
   const int rec_dtype = descs[0].record_dtype, map_dtype = descs[0].map_dtype;
   if (rec_dtype != EPO_F32 && rec_dtype != EPO_F16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown record dtype");
@@ -690,6 +716,18 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_pair_ij, np);
     ALLOC(S->d_pair_lw, np);
     ALLOC(S->d_pose_entries, (size_t)nv * S->pose_stride);
+    if (S->refine) {
+      ALLOC(S->d_gamma, nv);
+      ALLOC(S->d_K64r, (size_t)6 * nv);
+      ALLOC(S->d_pair_facc, (size_t)2 * np);
+      ALLOC(S->d_grad_gamma, nv);
+      const size_t nr = (size_t)std::max<int64_t>(S->n_records, 1);
+      ALLOC(S->d_alpha, nr);
+      ALLOC(S->d_beta, nr);
+      ALLOC(S->d_grad_z, nr);
+      ALLOC(S->d_grad_alpha, nr);
+      ALLOC(S->d_grad_beta, nr);
+    }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
     cudaStream_t st = S->stream;
     if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
@@ -757,6 +795,11 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       CK(cudaMemcpyAsync(S->d_loss_chunk_scene, chunk_scene.data(), chunk_scene.size() * 4, cudaMemcpyHostToDevice,
                          st));
     CK(cudaMemsetAsync(S->d_pair_acc, 0, (size_t)kAcc * np * 8, st));
+    if (S->refine) {
+      epo_status rs = epo_set_refinement(S, nullptr, nullptr, nullptr);  // identity: gamma 0, alpha 1, beta 0
+      if (rs != EPO_OK) return rs;
+      CK(cudaMemsetAsync(S->d_pair_facc, 0, (size_t)2 * np * 8, st));
+    }
     // validate maps on the device
     CK(launch_map_check(S->d_map, S->map_dtype, S->map_elems, S->d_flag, st));
     CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, st));
@@ -920,7 +963,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = 3;
+  info->kernels_per_step = S->refine ? 4 : 3;
   info->tail_pairs = S->tail;
   return EPO_OK;
 }
@@ -1019,6 +1062,7 @@ epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, nullptr);
   MARK(0, S->stream);
+  if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
   CK(launch_pair_setup(a, MODE_FWD, S->stream));
   MARK(1, S->stream);
   st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, S->stream);
@@ -1035,6 +1079,7 @@ epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* d
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, dloss_dev);
   MARK(0, S->stream);
+  if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
   CK(launch_pair_setup(a, MODE_BWD, S->stream));
   MARK(1, S->stream);
   epo_status st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, S->stream);
@@ -1118,6 +1163,60 @@ epo_status epo_step_plain(epo_scene_t S, int32_t n_steps) {
   return EPO_OK;
 }
 
+epo_status epo_set_refinement(epo_scene_t S, const double* gamma, const float* alpha, const float* beta) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
+  const size_t nv = (size_t)S->n_views, nr = (size_t)S->n_records;
+  std::vector<double> g(gamma ? gamma : nullptr, gamma ? gamma + nv : nullptr);
+  if (!gamma) g.assign(nv, 0.0);
+  for (double x : g)
+    if (!(x > -1.0) || !isfinite(x)) return fail(S, EPO_ERR_INVALID_ARG, "gamma must be finite and > -1");
+  std::vector<float> al(alpha ? alpha : nullptr, alpha ? alpha + nr : nullptr), be(beta ? beta : nullptr, beta ? beta + nr : nullptr);
+  if (!alpha) al.assign(nr, 1.f);
+  if (!beta) be.assign(nr, 0.f);
+  for (size_t r = 0; r < nr; ++r)
+    if (!isfinite(al[r]) || !isfinite(be[r])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite alpha or beta");
+  CK(cudaMemcpyAsync(S->d_gamma, g.data(), nv * 8, cudaMemcpyHostToDevice, S->stream));
+  if (nr) {
+    CK(cudaMemcpyAsync(S->d_alpha, al.data(), nr * 4, cudaMemcpyHostToDevice, S->stream));
+    CK(cudaMemcpyAsync(S->d_beta, be.data(), nr * 4, cudaMemcpyHostToDevice, S->stream));
+  }
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, double* grad_gamma, float* grad_alpha,
+                                    float* grad_beta) {
+  if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
+  epo_status st = maybe_autotune(S);
+  if (st != EPO_OK) return st;
+  cudaStream_t s = S->stream;
+  StepArgs a = step_args(S, S->d_T, nullptr);
+  // forward: the loss and every pair's valid count (the pair means' denominators)
+  CK(launch_refine_intrinsics(a, s));
+  CK(launch_pair_setup(a, MODE_FWD, s));
+  st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, s);
+  if (st != EPO_OK) return st;
+  CK(launch_poses(a, 0, s));
+  // adjoint: pose and focal sums per pair, dL/dz per record with the pairs' weights
+  CK(cudaMemsetAsync(S->d_grad_z, 0, (size_t)std::max<int64_t>(S->n_records, 1) * 4, s));
+  CK(launch_pair_setup(a, MODE_BWD, s));
+  st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, s);
+  if (st != EPO_OK) return st;
+  CK(launch_poses(a, 1, s));
+  CK(launch_depth_grads(S->d_rec, S->rec_dtype, S->d_grad_z, S->d_grad_alpha, S->d_grad_beta, S->n_records, s));
+  CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, s));
+  if (grad) CK(cudaMemcpyAsync(grad, S->d_grad, (size_t)S->n_views * 48, cudaMemcpyDeviceToHost, s));
+  if (grad_gamma) CK(cudaMemcpyAsync(grad_gamma, S->d_grad_gamma, (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, s));
+  if (grad_alpha && S->n_records)
+    CK(cudaMemcpyAsync(grad_alpha, S->d_grad_alpha, (size_t)S->n_records * 4, cudaMemcpyDeviceToHost, s));
+  if (grad_beta && S->n_records)
+    CK(cudaMemcpyAsync(grad_beta, S->d_grad_beta, (size_t)S->n_records * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return EPO_OK;
+}
+
 epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
   if (!S || n < 0 || (n > 0 && !ids)) return fail(S, EPO_ERR_INVALID_ARG, "invalid subset");
   std::vector<uint8_t> act(S->n_pairs, n == 0 ? 1 : 0);
@@ -1187,6 +1286,7 @@ epo_status epo_autotune(epo_scene_t S) {
       CK(launch_l2_read(flush, (int64_t)flush_bytes / 2, (unsigned*)((char*)flush + flush_bytes), S->sm_count,
                         S->stream));
     }
+    if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
     CK(launch_pair_setup(a, MODE_FUSED, S->stream));
     CK(cudaEventRecord(e0, S->stream));
     st = run_edge(S, MODE_FUSED, c.g, c.r, c.b, c.t, S->stream);

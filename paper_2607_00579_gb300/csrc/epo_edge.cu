@@ -113,6 +113,7 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 struct AmbEntry {
   float u, v, z;
   int p;
+  int64_t rec;  // the record (refine scenes reload its prior depth for an FP64 z)
 };
 constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
 
@@ -127,16 +128,24 @@ constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than 
 //     decision d <= lambda takes the FP32 value unless it lies within its error bound of
 //     lambda, in which case the fractions and d are formed again in FP64.
 // Adds straight to the pair's FP64 accumulators.
-template <int MODE, int MAP>
+template <int MODE, int REC, int MAP, int REF>
 __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, float lamf) {
   const int p = en.p;
   const int i = a.pair_src[p];
   const PairParam& P = a.pp[p];
+  // K64 holds fx, fy, cx, cy followed by 1/fx, 1/fy (refine scenes: at f0 (1 + gamma))
   const double* Ki = a.K64 + 6 * (size_t)i;
   const double* Kj = a.K64 + 6 * (size_t)a.pair_dst[p];
-  // K64 holds fx, fy, cx, cy followed by 1/fx, 1/fy
-  const double X[3] = {((double)en.u - Ki[2]) * Ki[4] * (double)en.z, ((double)en.v - Ki[3]) * Ki[5] * (double)en.z,
-                       (double)en.z};
+  double z = (double)en.z, u = (double)en.u, v = (double)en.v;
+  if constexpr (REF) {  // the record's pixel, and Z0 alpha + beta in FP64 as the definition has it
+    float u0, v0, z0;
+    load_record<REC>(a.rec, en.rec, u0, v0, z0);
+    u = (double)u0;
+    v = (double)v0;
+    z = fma((double)z0, (double)a.alpha[en.rec], (double)a.beta[en.rec]);
+  }
+  const double xt = (u - Ki[2]) * Ki[4], yt = (v - Ki[3]) * Ki[5];
+  const double X[3] = {xt * z, yt * z, z};
   const double* R = a.pp64 + 12 * (size_t)p;
   double Y[3];
 #pragma unroll
@@ -196,19 +205,41 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, fl
       atomicAdd(acc + 5, (double)(y1f * gz - y2f * gy));
       atomicAdd(acc + 6, (double)(y2f * gx - y0f * gz));
       atomicAdd(acc + 7, (double)(y0f * gy - y1f * gx));
+      if constexpr (REF) {
+        // R (x~, y~, 1) = dY/dz; dRho/dz = g . dY/dz; the focal terms as in the fast path
+        const float xtf = (float)xt, ytf = (float)yt, zf = (float)z;
+        const float* r = P.r;
+        const float dz = gx * fmaf(r[0], xtf, fmaf(r[1], ytf, r[2])) + gy * fmaf(r[3], xtf, fmaf(r[4], ytf, r[5])) +
+                         gz * fmaf(r[6], xtf, fmaf(r[7], ytf, r[8]));
+        const float gr2 = gx * r[2] + gy * r[5] + gz * r[8];
+        atomicAdd(a.pair_facc + 2 * (size_t)p, (double)(zf * (gr2 - dz)));
+        atomicAdd(a.pair_facc + 2 * (size_t)p + 1, (double)(gx * y0f + gy * y1f));
+        if constexpr (MODE == MODE_BWD) {
+          const double n = acc[1];
+          const float w = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
+          atomicAdd(a.grad_z + en.rec, w * dz);
+        }
+      }
     }
   }
 }
 
-template <int MODE, int REC, int MAP, int GATHER, int RPT>
+// Per-pair sums a warp reduces: the 8 of the pose gradient, plus the two focal sums of a
+// refine scene.
+template <int REF>
+__host__ __device__ constexpr int edge_slots() { return REF ? kAcc + 2 : kAcc; }
+
+template <int MODE, int REC, int MAP, int GATHER, int RPT, int REF>
 __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
-  // dynamic shared memory: lifted records of the tile, their raw (u, v), then every warp's
-  // partial sums per pair of the tile (summed in a fixed warp order at the flush, so the
-  // result does not depend on warp timing)
+  // dynamic shared memory: lifted records of the tile, their raw (u, v) (refine scenes:
+  // the unit-depth rays (x~, y~) instead), then every warp's partial sums per pair of the
+  // tile (summed in a fixed warp order at the flush, so the result does not depend on warp
+  // timing)
+  constexpr int NSLOT = edge_slots<REF>();
   extern __shared__ float4 s_dyn[];
   float4* s_X = s_dyn;                                                    // [blockDim * RPT]
   float2* s_UV = reinterpret_cast<float2*>(s_dyn + blockDim.x * RPT);    // [blockDim * RPT]
-  float* s_part = reinterpret_cast<float*>(s_UV + blockDim.x * RPT);     // [warps][max_pairs][8]
+  float* s_part = reinterpret_cast<float*>(s_UV + blockDim.x * RPT);     // [warps][max_pairs][NSLOT]
   __shared__ int s_tile, s_next;
   __shared__ int s_amb_n;
   __shared__ AmbEntry s_amb[kAmbCap];
@@ -231,6 +262,11 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     if (threadIdx.x == 0) s_next = atomicAdd(a.tile_counter, 1);
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
+    float vfx = vi.fx, vfy = vi.fy;
+    if constexpr (REF) {  // f = f0 (1 + gamma) (Eq. 4): the refined FP64 intrinsics, rounded
+      vfx = (float)a.K64[6 * (size_t)td.view];
+      vfy = (float)a.K64[6 * (size_t)td.view + 1];
+    }
     // a2: stream the tile's records (coalesced 128-bit loads), lift once per record into
     // shared memory; each thread reads back only its own records
 #pragma unroll
@@ -238,17 +274,31 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       const int idx = threadIdx.x + r * blockDim.x;
       float u = 0.f, v = 0.f, z = 0.f;
       if (idx < td.n) load_record<REC>(a.rec, td.begin + idx, u, v, z);
-      const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
-      // rounding-error bound of Y = R X + t: 6u|X|_1 (rotation, lift and FMA roundings);
-      // a record past the tile end gets w < 0 and is skipped
-      const float XA = idx < td.n ? 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
-      s_X[idx] = make_float4(X0, X1, z, XA);
-      s_UV[idx] = make_float2(u, v);
+      if constexpr (REF) {  // z = Z0 alpha + beta (Eq. 5)
+        if (idx < td.n) z = fmaf(z, a.alpha[td.begin + idx], a.beta[td.begin + idx]);
+        const float xt = (u - vi.cx) / vfx, yt = (v - vi.cy) / vfy;
+        const float X0 = xt * z, X1 = yt * z;
+        // rounding-error bound of Y = R X + t: 8u|X|_1 (rotation, lift, the rounded refined
+        // focal length and depth, FMA roundings)
+        const float XA = idx < td.n ? 8.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
+        s_X[idx] = make_float4(X0, X1, z, XA);
+        s_UV[idx] = make_float2(xt, yt);
+      } else {
+        const float X0 = (u - vi.cx) / vfx * z, X1 = (v - vi.cy) / vfy * z;
+        // rounding-error bound of Y = R X + t: 6u|X|_1 (rotation, lift and FMA roundings);
+        // a record past the tile end gets w < 0 and is skipped
+        const float XA = idx < td.n ? 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
+        s_X[idx] = make_float4(X0, X1, z, XA);
+        s_UV[idx] = make_float2(u, v);
+      }
     }
     // the item's pair range, loaded where it is needed (holding the whole item in
     // registers across the pair loop costs a block per SM)
     const int pb = __ldg(&a.tiles[t].q0);
     const int pe = __ldg(&a.tiles[t].q1);
+    float gzr[REF && MODE == MODE_BWD ? RPT : 1];  // refine adjoint: dL/dz of the thread's records
+#pragma unroll
+    for (int r = 0; r < (REF && MODE == MODE_BWD ? RPT : 1); ++r) gzr[r] = 0.f;
     for (int q = pb; q < pe; ++q) {
       const int p = a.src_pair_ids[q];
       if (!a.pair_active[p]) continue;  // uniform over the block
@@ -257,6 +307,12 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       float acc[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+      float facc0 = 0.f, facc1 = 0.f;  // refine: source- and target-focal sums
+      float wp = 0.f;                  // refine adjoint: the pair's weight in the loss
+      if constexpr (REF && MODE == MODE_BWD) {
+        const double n = a.pair_acc[(size_t)kAcc * p + 1];  // valid samples, from the forward pass
+        wp = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
+      }
       // the thread's RPT records, ILP of them in flight at a time: one reduction per pair
       // for all RPT samples, registers for only ILP
       constexpr int ILP = RPT < 2 ? RPT : 2;
@@ -335,8 +391,8 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
               const int pos = base + __popc(bal & lanemask_lt);
               if (pos < kAmbCap) {
                 const int li = threadIdx.x + (g + r) * blockDim.x;
-                const float2 uv = s_UV[li];
-                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
+                const float2 uv = s_UV[li];  // refine scenes: reloaded from the record
+                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p, REF ? td.begin + li : (int64_t)0};
               } else {
                 // buffer full: evaluate this sample with FP32 decisions instead
                 atomicAdd(a.q_overflow, 1u);
@@ -376,33 +432,67 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
               acc[5] += Y1[r] * gz - Y2[r] * gy;
               acc[6] += Y2[r] * gx - Y0[r] * gz;
               acc[7] += Y0[r] * gy - Y1[r] * gx;
+              if constexpr (REF) {
+                // dY/dz = R (x~, y~, 1): dRho/dz = g . dY/dz; the source focal term
+                // -g . R (X0, X1, 0) = z (g . r_2 - dRho/dz) (times 1 + gamma_i) and the
+                // target focal term gx Y0 + gy Y1 (times 1 + gamma_j)
+                const int li = threadIdx.x + (g + r) * blockDim.x;
+                const float2 xy = s_UV[li];
+                const float zr = s_X[li].z;
+                const float dz = gx * fmaf(P.r[0], xy.x, fmaf(P.r[1], xy.y, P.r[2])) +
+                                 gy * fmaf(P.r[3], xy.x, fmaf(P.r[4], xy.y, P.r[5])) +
+                                 gz * fmaf(P.r[6], xy.x, fmaf(P.r[7], xy.y, P.r[8]));
+                const float gr2 = gx * P.r[2] + gy * P.r[5] + gz * P.r[8];
+                facc0 += zr * (gr2 - dz);
+                facc1 += gx * Y0[r] + gy * Y1[r];
+                if constexpr (MODE == MODE_BWD) gzr[g + r] += wp * dz;
+              }
             }
           }
         }
       }
       // a7: warp reduce-scatter; lanes 0..7 store the warp's 8 sums (no block barrier)
       const float sred = warp_reduce_scatter8(acc, lane);
-      if (lane < 8) s_part[((size_t)warp * a.max_pairs + (q - pb)) * kAcc + scatter_slot(lane)] = sred;
+      if (lane < 8) s_part[((size_t)warp * a.max_pairs + (q - pb)) * NSLOT + scatter_slot(lane)] = sred;
+      if constexpr (REF && MODE != MODE_FWD) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          facc0 += __shfl_xor_sync(0xffffffffu, facc0, o);
+          facc1 += __shfl_xor_sync(0xffffffffu, facc1, o);
+        }
+        if (lane == 8 || lane == 9)
+          s_part[((size_t)warp * a.max_pairs + (q - pb)) * NSLOT + lane] = lane == 8 ? facc0 : facc1;
+      }
+    }
+    if constexpr (REF && MODE == MODE_BWD) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int idx = threadIdx.x + r * blockDim.x;
+        if (idx < td.n && gzr[r] != 0.f) atomicAdd(a.grad_z + td.begin + idx, gzr[r]);
+      }
     }
     __syncthreads();  // every warp has stored its partial sums for this tile
     // flush: warps summed in a fixed order, one FP64 atomic per used pair slot
     constexpr int S0 = MODE == MODE_BWD ? 2 : 0;
-    constexpr int NS = MODE == MODE_FWD ? 2 : (MODE == MODE_BWD ? 6 : 8);
+    constexpr int NS = MODE == MODE_FWD ? 2 : NSLOT - S0;
     const int nq = (pe - pb) * NS;
     for (int k = threadIdx.x; k < nq; k += blockDim.x) {
       const int qq = k / NS, slot = S0 + k % NS;
       const int p = a.src_pair_ids[pb + qq];
       if (!a.pair_active[p]) continue;
       float s = 0.f;
-      for (int w = 0; w < nwarp; ++w) s += s_part[((size_t)w * a.max_pairs + qq) * kAcc + slot];
-      if (s != 0.f) atomicAdd(a.pair_acc + (size_t)kAcc * p + slot, (double)s);
+      for (int w = 0; w < nwarp; ++w) s += s_part[((size_t)w * a.max_pairs + qq) * NSLOT + slot];
+      if (s != 0.f) {
+        if (slot < kAcc) atomicAdd(a.pair_acc + (size_t)kAcc * p + slot, (double)s);
+        else atomicAdd(a.pair_facc + 2 * (size_t)p + (slot - kAcc), (double)s);
+      }
     }
     if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
     // exact path: when the buffer is more than half full, and once more before exiting
     const int n_amb = min(s_amb_n, kAmbCap);
     if (n_amb > (s_tile < a.n_tiles ? kAmbCap / 2 : 0)) {
-      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, MAP>(a, s_amb[k], lam64, lam);
+      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, REC, MAP, REF>(a, s_amb[k], lam64, lam);
       __syncthreads();
       if (threadIdx.x == 0) {
         atomicAdd(a.q_count, (unsigned)n_amb);
@@ -413,90 +503,135 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   }
 }
 
-size_t edge_smem_bytes(int rpt, int block, int max_pairs) {
-  // dynamic part: lifted records, raw (u, v), per-warp per-pair partial sums
-  return sizeof(float4) * (size_t)rpt * block + sizeof(float2) * (size_t)rpt * block +
-         sizeof(float) * kAcc * (size_t)max_pairs * (block / 32);
+// dL/dalpha_r = dL/dz_r Z0_r and dL/dbeta_r = dL/dz_r (z_r = Z0_r alpha_r + beta_r, Eq. 5).
+template <int REC>
+__global__ void k_depth_grads(const void* rec, const float* grad_z, float* grad_alpha, float* grad_beta, int64_t n) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    float u, v, z0;
+    load_record<REC>(rec, r, u, v, z0);
+    const float gz = grad_z[r];
+    if (grad_alpha) grad_alpha[r] = gz * z0;
+    if (grad_beta) grad_beta[r] = gz;
+  }
 }
 
-template <int MODE, int REC, int MAP, int GATHER, int R>
-static cudaError_t launch_edge_one(const EdgeArgs& a, int block, int grid, cudaStream_t s) {
-  const size_t smem = edge_smem_bytes(R, block, a.max_pairs);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_edge<MODE, REC, MAP, GATHER, R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_edge<MODE, REC, MAP, GATHER, R><<<grid, block, smem, s>>>(a);
+cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
+                               float* grad_beta, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (rec_dtype) k_depth_grads<1><<<nb, 256, 0, s>>>(rec, grad_z, grad_alpha, grad_beta, n);
+  else k_depth_grads<0><<<nb, 256, 0, s>>>(rec, grad_z, grad_alpha, grad_beta, n);
   return cudaGetLastError();
 }
 
-template <int MODE, int REC, int MAP, int GATHER>
+size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine) {
+  // dynamic part: lifted records, raw (u, v), per-warp per-pair partial sums
+  return sizeof(float4) * (size_t)rpt * block + sizeof(float2) * (size_t)rpt * block +
+         sizeof(float) * (refine ? edge_slots<1>() : edge_slots<0>()) * (size_t)max_pairs * (block / 32);
+}
+
+template <int MODE, int REC, int MAP, int GATHER, int R, int REF>
+static cudaError_t launch_edge_one(const EdgeArgs& a, int block, int grid, cudaStream_t s) {
+  const size_t smem = edge_smem_bytes(R, block, a.max_pairs, REF);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_edge<MODE, REC, MAP, GATHER, R, REF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_edge<MODE, REC, MAP, GATHER, R, REF><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Refine scenes run two records per thread only (one set of instantiations).
+template <int MODE, int REC, int MAP, int GATHER, int REF>
 static cudaError_t launch_edge_rpt(const EdgeArgs& a, int rpt, int block, int grid, cudaStream_t s) {
-  switch (rpt) {
-    case 1: return launch_edge_one<MODE, REC, MAP, GATHER, 1>(a, block, grid, s);
-    case 2: return launch_edge_one<MODE, REC, MAP, GATHER, 2>(a, block, grid, s);
-    case 4: return launch_edge_one<MODE, REC, MAP, GATHER, 4>(a, block, grid, s);
-    default: return cudaErrorInvalidValue;
+  if constexpr (REF) {
+    if (rpt != 2) return cudaErrorInvalidValue;
+    return launch_edge_one<MODE, REC, MAP, GATHER, 2, 1>(a, block, grid, s);
+  } else {
+    switch (rpt) {
+      case 1: return launch_edge_one<MODE, REC, MAP, GATHER, 1, 0>(a, block, grid, s);
+      case 2: return launch_edge_one<MODE, REC, MAP, GATHER, 2, 0>(a, block, grid, s);
+      case 4: return launch_edge_one<MODE, REC, MAP, GATHER, 4, 0>(a, block, grid, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 
-template <int MODE, int REC, int MAP>
+template <int MODE, int REC, int MAP, int REF>
 static cudaError_t launch_edge_g(const EdgeArgs& a, int gather, int rpt, int block, int grid,
                                  cudaStream_t s) {
-  if (gather == GATHER_TEX) return launch_edge_rpt<MODE, REC, MAP, GATHER_TEX>(a, rpt, block, grid, s);
-  return launch_edge_rpt<MODE, REC, MAP, GATHER_LDG>(a, rpt, block, grid, s);
+  if (gather == GATHER_TEX) return launch_edge_rpt<MODE, REC, MAP, GATHER_TEX, REF>(a, rpt, block, grid, s);
+  return launch_edge_rpt<MODE, REC, MAP, GATHER_LDG, REF>(a, rpt, block, grid, s);
+}
+
+template <int MODE, int REF>
+static cudaError_t launch_edge_m(const EdgeArgs& a, int rec, int map, int gather, int rpt, int block,
+                                 int grid, cudaStream_t s) {
+  if (rec == 0 && map == 0) return launch_edge_g<MODE, 0, 0, REF>(a, gather, rpt, block, grid, s);
+  if (rec == 0 && map == 1) return launch_edge_g<MODE, 0, 1, REF>(a, gather, rpt, block, grid, s);
+  if (rec == 1 && map == 0) return launch_edge_g<MODE, 1, 0, REF>(a, gather, rpt, block, grid, s);
+  return launch_edge_g<MODE, 1, 1, REF>(a, gather, rpt, block, grid, s);
 }
 
 template <int MODE>
-static cudaError_t launch_edge_m(const EdgeArgs& a, int rec, int map, int gather, int rpt, int block,
+static cudaError_t launch_edge_r(const EdgeArgs& a, int refine, int rec, int map, int gather, int rpt, int block,
                                  int grid, cudaStream_t s) {
-  if (rec == 0 && map == 0) return launch_edge_g<MODE, 0, 0>(a, gather, rpt, block, grid, s);
-  if (rec == 0 && map == 1) return launch_edge_g<MODE, 0, 1>(a, gather, rpt, block, grid, s);
-  if (rec == 1 && map == 0) return launch_edge_g<MODE, 1, 0>(a, gather, rpt, block, grid, s);
-  return launch_edge_g<MODE, 1, 1>(a, gather, rpt, block, grid, s);
+  if (refine) return launch_edge_m<MODE, 1>(a, rec, map, gather, rpt, block, grid, s);
+  return launch_edge_m<MODE, 0>(a, rec, map, gather, rpt, block, grid, s);
 }
 
 // rec_dtype: 0 = f32 records, 1 = f16-depth records; map_dtype: 0 = f32, 1 = bf16.
-cudaError_t launch_edge(const EdgeArgs& a, int mode, int rec_dtype, int map_dtype, int gather,
+cudaError_t launch_edge(const EdgeArgs& a, int mode, int refine, int rec_dtype, int map_dtype, int gather,
                         int rpt, int block, int grid, cudaStream_t s) {
   if (a.n_tiles == 0) return cudaSuccess;
   switch (mode) {
-    case MODE_FWD: return launch_edge_m<MODE_FWD>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
-    case MODE_BWD: return launch_edge_m<MODE_BWD>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
-    default: return launch_edge_m<MODE_FUSED>(a, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+    case MODE_FWD: return launch_edge_r<MODE_FWD>(a, refine, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+    case MODE_BWD: return launch_edge_r<MODE_BWD>(a, refine, rec_dtype, map_dtype, gather, rpt, block, grid, s);
+    default: return launch_edge_r<MODE_FUSED>(a, refine, rec_dtype, map_dtype, gather, rpt, block, grid, s);
   }
 }
 
-template <int MODE, int REC, int MAP, int GATHER>
+template <int MODE, int REC, int MAP, int GATHER, int REF>
 static const void* edge_ptr_rpt(int rpt) {
-  switch (rpt) {
-    case 1: return (const void*)k_edge<MODE, REC, MAP, GATHER, 1>;
-    case 2: return (const void*)k_edge<MODE, REC, MAP, GATHER, 2>;
-    case 4: return (const void*)k_edge<MODE, REC, MAP, GATHER, 4>;
-    default: return nullptr;
+  if constexpr (REF) {
+    return rpt == 2 ? (const void*)k_edge<MODE, REC, MAP, GATHER, 2, 1> : nullptr;
+  } else {
+    switch (rpt) {
+      case 1: return (const void*)k_edge<MODE, REC, MAP, GATHER, 1, 0>;
+      case 2: return (const void*)k_edge<MODE, REC, MAP, GATHER, 2, 0>;
+      case 4: return (const void*)k_edge<MODE, REC, MAP, GATHER, 4, 0>;
+      default: return nullptr;
+    }
   }
 }
 
-template <int MODE>
+template <int MODE, int REF>
 static const void* edge_ptr_m(int rec, int map, int gather, int rpt) {
   if (gather == GATHER_TEX) {
-    if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_TEX>(rpt);
-    if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_TEX>(rpt);
-    if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_TEX>(rpt);
-    return edge_ptr_rpt<MODE, 1, 1, GATHER_TEX>(rpt);
+    if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_TEX, REF>(rpt);
+    if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_TEX, REF>(rpt);
+    if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_TEX, REF>(rpt);
+    return edge_ptr_rpt<MODE, 1, 1, GATHER_TEX, REF>(rpt);
   }
-  if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_LDG>(rpt);
-  if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_LDG>(rpt);
-  if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_LDG>(rpt);
-  return edge_ptr_rpt<MODE, 1, 1, GATHER_LDG>(rpt);
+  if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_LDG, REF>(rpt);
+  if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_LDG, REF>(rpt);
+  if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_LDG, REF>(rpt);
+  return edge_ptr_rpt<MODE, 1, 1, GATHER_LDG, REF>(rpt);
 }
 
-const void* edge_kernel_ptr(int mode, int rec_dtype, int map_dtype, int gather, int rpt) {
+const void* edge_kernel_ptr(int mode, int refine, int rec_dtype, int map_dtype, int gather, int rpt) {
+  if (refine) {
+    switch (mode) {
+      case MODE_FWD: return edge_ptr_m<MODE_FWD, 1>(rec_dtype, map_dtype, gather, rpt);
+      case MODE_BWD: return edge_ptr_m<MODE_BWD, 1>(rec_dtype, map_dtype, gather, rpt);
+      default: return edge_ptr_m<MODE_FUSED, 1>(rec_dtype, map_dtype, gather, rpt);
+    }
+  }
   switch (mode) {
-    case MODE_FWD: return edge_ptr_m<MODE_FWD>(rec_dtype, map_dtype, gather, rpt);
-    case MODE_BWD: return edge_ptr_m<MODE_BWD>(rec_dtype, map_dtype, gather, rpt);
-    default: return edge_ptr_m<MODE_FUSED>(rec_dtype, map_dtype, gather, rpt);
+    case MODE_FWD: return edge_ptr_m<MODE_FWD, 0>(rec_dtype, map_dtype, gather, rpt);
+    case MODE_BWD: return edge_ptr_m<MODE_BWD, 0>(rec_dtype, map_dtype, gather, rpt);
+    default: return edge_ptr_m<MODE_FUSED, 0>(rec_dtype, map_dtype, gather, rpt);
   }
 }
 

@@ -96,6 +96,14 @@ struct EdgeArgs {
   int32_t max_pairs;             // most outgoing pairs of any view (shared accumulators)
   float delta;
   float eps_z;
+  // focal and depth refinement (scenes created with refine = 1; Eqs. 4-5)
+  const double* gamma;           // n_views: f = f0 (1 + gamma)
+  const float* alpha;            // n_records: z = z0 alpha + beta
+  const float* beta;
+  double* pair_facc;             // n_pairs x 2: sums of the source- and target-focal terms
+  float* grad_z;                 // n_records: dL/dz (adjoint pass only)
+  const double* pair_lw;         // n_pairs: the pair's weight in its scene's loss
+  int32_t norm_all;
 };
 
 // One (pair, role) entry of a pose's gradient gather, laid out at a fixed stride per pose so
@@ -110,6 +118,14 @@ struct PoseEntry {
 
 struct StepArgs {
   int32_t n_views, n_pairs, n_scenes;
+  // focal refinement (refine scenes): gamma per view, the FP64 base intrinsics and their
+  // refined copy written by the pair setup, the per-pair focal sums and the focal gradient
+  int32_t refine;
+  const double* gamma;
+  const double* K64;                 // n_views x 6: fx, fy, cx, cy, 1/fx, 1/fy (base)
+  double* K64r;                      // the same at f0 (1 + gamma)
+  double* pair_facc;                 // n_pairs x 2
+  double* grad_gamma;                // n_views
   const unsigned long long* tex;     // n_views texture objects (copied into PairParam)
   const int32_t* pair_src;
   const int32_t* pair_dst;
@@ -157,8 +173,11 @@ struct StepArgs {
 
 // ---- launchers (epo_kernels.cu) ----
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
+                               float* grad_beta, int64_t n, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);
-cudaError_t launch_edge(const EdgeArgs& a, int mode, int rec_dtype, int map_dtype, int gather,
+cudaError_t launch_edge(const EdgeArgs& a, int mode, int refine, int rec_dtype, int map_dtype, int gather,
                         int rpt, int block, int grid, cudaStream_t s);
 // pose kernel: with_grad 0 = loss only, 1 = loss + gradient, 2 = + Adam/Exp update
 cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s);
@@ -170,7 +189,7 @@ cudaError_t launch_map_check(const void* map, int dtype, int64_t n, int32_t* bad
 cudaError_t launch_edt(const uint8_t* edges, int W, int H, float* map, cudaStream_t s);
 cudaError_t launch_round_bf16(const float* src, uint16_t* dst, int64_t n, cudaStream_t s);
 int edt_max_height();
-const void* edge_kernel_ptr(int mode, int rec_dtype, int map_dtype, int gather, int rpt);
-size_t edge_smem_bytes(int rpt, int block, int max_pairs);
+const void* edge_kernel_ptr(int mode, int refine, int rec_dtype, int map_dtype, int gather, int rpt);
+size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine);
 
 }  // namespace epo

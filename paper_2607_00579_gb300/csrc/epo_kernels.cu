@@ -85,10 +85,38 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
     of[e] = vf;
   } else if (e == 15) {
     out->Et = 4.f * kU32 * (fabsf(t0) + fabsf(t1) + fabsf(t2));
+  } else if (a.refine && e == 12) {
+    // refine scenes: the target's intrinsics at f0 (1 + gamma_j) (Eq. 4), rounded to FP32;
+    // the projection bound grows by one rounding of the focal length
+    const double sc = 1.0 + a.gamma[j];
+    const float fx = (float)(a.K64[6 * (size_t)j] * sc), fy = (float)(a.K64[6 * (size_t)j + 1] * sc);
+    out->fx = fx;
+    out->fy = fy;
+    out->fx2 = 2.f * fx;
+    out->fy2 = 2.f * fy;
+    out->cu = 5.f * kU32 * (float)(out->W + 1);
+    out->cv = 5.f * kU32 * (float)(out->H + 1);
   }
   if (e < kAcc) {
     const bool zero = (e < 2) ? (mode != MODE_BWD) : (mode != MODE_FWD);
     if (zero) a.pair_acc[(size_t)kAcc * p + e] = 0.0;
+  }
+  if (a.refine && mode != MODE_FWD && (e == 8 || e == 9)) a.pair_facc[2 * (size_t)p + e - 8] = 0.0;
+}
+
+// Refine scenes: the FP64 intrinsics at f0 (1 + gamma) of every view (fx, fy, cx, cy, 1/fx,
+// 1/fy), read by the edge kernel's lift and exact path.
+__global__ void k_refine_intrinsics(StepArgs a) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n_views; v += gridDim.x * blockDim.x) {
+    const double sc = 1.0 + a.gamma[v];
+    const double fx = a.K64[6 * (size_t)v] * sc, fy = a.K64[6 * (size_t)v + 1] * sc;
+    double* K = a.K64r + 6 * (size_t)v;
+    K[0] = fx;
+    K[1] = fy;
+    K[2] = a.K64[6 * (size_t)v + 2];
+    K[3] = a.K64[6 * (size_t)v + 3];
+    K[4] = 1.0 / fx;
+    K[5] = 1.0 / fy;
   }
 }
 
@@ -144,6 +172,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       bp1 = a.bpow[1];
     }
     double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double gg = 0.0;  // refine scenes: dL/dgamma_v, before the 1 / (1 + gamma_v) factor
     if (vv) {
       const PoseEntry* ent = a.pose_entries + (size_t)v * a.pose_stride;
       for (int k = e; k < a.pose_stride; k += 16) {
@@ -160,6 +189,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         if (a.gscale) c *= a.gscale[en.scene_role >> 1];
         const double ga0 = c * acc[2], ga1 = c * acc[3], ga2 = c * acc[4];
         const double gb0 = c * acc[5], gb1 = c * acc[6], gb2 = c * acc[7];
+        if (a.refine) gg += c * a.pair_facc[2 * (size_t)p + ((en.scene_role & 1) ? 0 : 1)];
         if ((en.scene_role & 1) == 0) {  // target view j: the 6-vector as is
           g[0] += ga0; g[1] += ga1; g[2] += ga2;
           g[3] += gb0; g[4] += gb1; g[5] += gb2;
@@ -179,9 +209,12 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     }
     // fixed-order reduction over the 16 lanes of the pose
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1)
+    for (int o = 8; o > 0; o >>= 1) {
 #pragma unroll
       for (int k = 0; k < 6; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
+      if (a.refine) gg += __shfl_xor_sync(0xffffffffu, gg, o);
+    }
+    if (a.refine && vv && e == 0 && a.grad_gamma) a.grad_gamma[v] = gg / (1.0 + a.gamma[v]);
     double G = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k)
@@ -505,6 +538,11 @@ __global__ void k_round_bf16(const float* src, uint16_t* dst, int64_t n) {
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
+cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s) {
+  k_refine_intrinsics<<<std::max((a.n_views + 127) / 128, 1), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s) {
   const int nb = std::max((a.n_pairs * kSetupLanes + kSetupThreads - 1) / kSetupThreads, 1);
   k_pair_setup<<<nb, kSetupThreads, 0, s>>>(a, mode);
