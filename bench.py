@@ -487,6 +487,8 @@ def run_ours(args):
         line["plain_per_scene"] = leg
     elif wl.key == "ring500":
         line["fp32_form"] = fp32_form_leg(epo, torch, wl, s, scene, lr, evals, args, flush_l2, stream)
+    elif wl.key == "ring32":
+        line["refine"] = refine_leg(epo, torch, wl, parts, (rd, md), lr, evals, args, flush_l2)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -524,6 +526,36 @@ def gather_roofline(epo, wl, info, evals, kern_ms, hbm_peak):
 
 
 ACC_STEPS = 100  # optimisation steps behind the final-accuracy comparisons
+
+
+def refine_leg(epo, torch, wl, parts, dtypes, lr, evals, args, flush_l2):
+    """Focal and per-pixel depth refinement (Eqs. 4-5): the objective with its gradient for
+    the poses, the focal scales and every edge pixel's depth parameters, through the public
+    call (two passes over the samples, host outputs), at a random small refinement."""
+    h = epo.Scene(parts, record_dtype=dtypes[0], map_dtype=dtypes[1],
+                  options=epo.default_options(refine=1, **lr), on_device=True)
+    h.set_poses(wl.T_init)
+    info = h.info()
+    rng = np.random.default_rng(0)
+    epo._binding.epo_set_refinement(h.handle, rng.normal(0, 0.005, info.n_views),
+                                    1.0 + rng.normal(0, 0.005, info.n_records).astype(np.float32),
+                                    rng.normal(0, 0.02, info.n_records).astype(np.float32))
+    call = lambda: epo._binding.epo_refine_loss_and_grad(h.handle, info.n_scenes, info.n_views, info.n_records)
+    for _ in range(3):
+        call()
+    n = max(5, min(args.steps, 50))
+    tot = 0.0
+    for k in range(n):
+        flush_l2(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        call()
+        tot += time.perf_counter() - t0
+    ms = 1e3 * tot / n
+    return {"value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_evaluation": ms, "iterations": n,
+            "passes_per_evaluation": 2, "kernels_per_evaluation": 8,
+            "d2h_bytes_per_evaluation": int(8 * info.n_scenes + 56 * info.n_views + 8 * info.n_records),
+            "note": "wall time of epo_refine_loss_and_grad (forward, adjoint, host copies of all gradients)"}
 
 
 def autograd_leg(epo, torch, s, T_init, evals, args, flush_l2, stream):

@@ -113,7 +113,6 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 struct AmbEntry {
   float u, v, z;
   int p;
-  int64_t rec;  // the record (refine scenes reload its prior depth for an FP64 z)
 };
 constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
 
@@ -128,8 +127,9 @@ constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than 
 //     decision d <= lambda takes the FP32 value unless it lies within its error bound of
 //     lambda, in which case the fractions and d are formed again in FP64.
 // Adds straight to the pair's FP64 accumulators.
+// rec: the sample's record (refine scenes reload its pixel and prior depth for an FP64 z).
 template <int MODE, int REC, int MAP, int REF>
-__device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, float lamf) {
+__device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, double lam, float lamf) {
   const int p = en.p;
   const int i = a.pair_src[p];
   const PairParam& P = a.pp[p];
@@ -139,10 +139,10 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, fl
   double z = (double)en.z, u = (double)en.u, v = (double)en.v;
   if constexpr (REF) {  // the record's pixel, and Z0 alpha + beta in FP64 as the definition has it
     float u0, v0, z0;
-    load_record<REC>(a.rec, en.rec, u0, v0, z0);
+    load_record<REC>(a.rec, rec, u0, v0, z0);
     u = (double)u0;
     v = (double)v0;
-    z = fma((double)z0, (double)a.alpha[en.rec], (double)a.beta[en.rec]);
+    z = fma((double)z0, (double)a.alpha[rec], (double)a.beta[rec]);
   }
   const double xt = (u - Ki[2]) * Ki[4], yt = (v - Ki[3]) * Ki[5];
   const double X[3] = {xt * z, yt * z, z};
@@ -217,7 +217,7 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, double lam, fl
         if constexpr (MODE == MODE_BWD) {
           const double n = acc[1];
           const float w = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
-          atomicAdd(a.grad_z + en.rec, w * dz);
+          atomicAdd(a.grad_z + rec, w * dz);
         }
       }
     }
@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   __shared__ int s_tile, s_next;
   __shared__ int s_amb_n;
   __shared__ AmbEntry s_amb[kAmbCap];
+  __shared__ int64_t s_amb_rec[REF ? kAmbCap : 1];  // refine scenes: the entries' records
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarp = blockDim.x >> 5;
@@ -392,7 +393,8 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
               if (pos < kAmbCap) {
                 const int li = threadIdx.x + (g + r) * blockDim.x;
                 const float2 uv = s_UV[li];  // refine scenes: reloaded from the record
-                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p, REF ? td.begin + li : (int64_t)0};
+                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
+                if constexpr (REF) s_amb_rec[pos] = td.begin + li;
               } else {
                 // buffer full: evaluate this sample with FP32 decisions instead
                 atomicAdd(a.q_overflow, 1u);
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     // exact path: when the buffer is more than half full, and once more before exiting
     const int n_amb = min(s_amb_n, kAmbCap);
     if (n_amb > (s_tile < a.n_tiles ? kAmbCap / 2 : 0)) {
-      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, REC, MAP, REF>(a, s_amb[k], lam64, lam);
+      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, REC, MAP, REF>(a, s_amb[k], REF ? s_amb_rec[k] : (int64_t)0, lam64, lam);
       __syncthreads();
       if (threadIdx.x == 0) {
         atomicAdd(a.q_count, (unsigned)n_amb);
