@@ -60,7 +60,8 @@ class _Opt(ctypes.Structure):
                 ("lambda_steps", ctypes.c_int), ("delta", ctypes.c_double),
                 ("eps_z", ctypes.c_double), ("norm_mode", ctypes.c_int),
                 ("lr_rot", ctypes.c_double), ("lr_trans", ctypes.c_double),
-                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("pair_budget", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 def _load():
@@ -84,6 +85,11 @@ def _load():
         lib.oracle_lambda.restype = ctypes.c_double
         lib.oracle_optimize.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int, P, P, P]
         lib.oracle_loss_grad_full.argtypes = [P] * 11
+        lib.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+        lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_pair_key.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32]
+        lib.oracle_pair_key.restype = ctypes.c_uint64
+        lib.oracle_subsample.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -221,7 +227,8 @@ class OracleScene:
 
     def optimize(self, T: np.ndarray, fixed: np.ndarray, n_steps: int, *, lambda0=10.0, lambda1=6.0,
                  lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID, lr_rot=1e-3,
-                 lr_trans=1e-2, beta1=0.9, beta2=0.999, eps=1e-12, step0=0, m=None, v=None):
+                 lr_trans=1e-2, beta1=0.9, beta2=0.999, eps=1e-12, step0=0, m=None, v=None, pair_budget=0,
+                 seed=0):
         """Run n_steps of Algorithm 2 (pose-only, tangent-space Adam).  Returns (T, m, v, losses)."""
         T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.n_views, 12).copy()
         fx = np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -229,12 +236,31 @@ class OracleScene:
         v = np.zeros((self.n_views, 6)) if v is None else np.ascontiguousarray(v, np.float64).copy()
         hist = np.zeros(max(n_steps, 1))
         opt = _Opt(lambda0, lambda1, lambda_steps, delta, eps_z, norm_mode, lr_rot, lr_trans, beta1,
-                   beta2, eps)
+                   beta2, eps, pair_budget, seed & (2**64 - 1))
         rc = _load().oracle_optimize(ctypes.byref(self._s), _p(T), _p(fx), ctypes.byref(opt), step0,
                                      n_steps, _p(m), _p(v), _p(hist))
         if rc:
             raise ValueError(f"oracle_optimize failed ({rc})")
         return T, m, v, hist[:n_steps]
+
+
+def splitmix64(state: int) -> int:
+    """SplitMix64's output for a state (the increment added first)."""
+    return int(_load().oracle_splitmix64(ctypes.c_uint64(state & (2**64 - 1))))
+
+
+def pair_key(seed: int, step: int, p: int) -> int:
+    return int(_load().oracle_pair_key(ctypes.c_uint64(seed & (2**64 - 1)), step, p))
+
+
+def subsample(seed: int, step: int, n_pairs: int, M: int) -> np.ndarray:
+    """Pairs of one scene evaluated at a step (Algorithm 3's fresh uniform subset of
+    min(|E|, M)): boolean mask over the scene's pairs."""
+    out = np.zeros(max(n_pairs, 1), dtype=np.uint8)
+    rc = _load().oracle_subsample(ctypes.c_uint64(seed & (2**64 - 1)), step, n_pairs, M, _p(out))
+    if rc:
+        raise ValueError(f"oracle_subsample failed ({rc})")
+    return out[:n_pairs].astype(bool)
 
 
 def set_threads(n: int = 0) -> int:

@@ -368,6 +368,47 @@ int oracle_loss_grad(const oracle_scene* S, const double* T, const oracle_params
 }
 
 /* ------------------------------------------------------------------ */
+/* Stochastic viewgraph sub-sampling (Appendix A.3, Algorithm 3): a fresh */
+/* uniform random subset of min(|E|, M) pairs every step.               */
+/* ------------------------------------------------------------------ */
+/* SplitMix64's output function (Steele, Lea and Flood, "Fast splittable pseudorandom
+ * number generators", OOPSLA 2014) applied to state + the golden-ratio increment. */
+uint64_t oracle_splitmix64(uint64_t state) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* The random key of pair p (index within its scene) at step s: one counter per (s, p). */
+uint64_t oracle_pair_key(uint64_t seed, int64_t step, int32_t p) {
+  return oracle_splitmix64(seed ^ (((uint64_t)step << 32) | (uint32_t)p));
+}
+
+/* The pairs of one scene evaluated at step s: the M with the smallest keys (ties by index),
+ * all of them when the scene has at most M.  active: n_pairs bytes (1 = evaluated). */
+int oracle_subsample(uint64_t seed, int64_t step, int32_t n_pairs, int32_t M, uint8_t* active) {
+  if (n_pairs < 0 || M < 0 || (n_pairs > 0 && !active)) return ORACLE_EINVAL;
+  for (int32_t p = 0; p < n_pairs; ++p) active[p] = 0;
+  if (n_pairs <= M) {
+    for (int32_t p = 0; p < n_pairs; ++p) active[p] = 1;
+    return ORACLE_OK;
+  }
+  /* selection by repeated minimum: plain and slow, for the small scenes of the tests */
+  uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n_pairs);
+  if (!key) return ORACLE_ENOMEM;
+  for (int32_t p = 0; p < n_pairs; ++p) key[p] = oracle_pair_key(seed, step, p);
+  for (int32_t m = 0; m < M; ++m) {
+    int32_t best = -1;
+    for (int32_t p = 0; p < n_pairs; ++p)
+      if (!active[p] && (best < 0 || key[p] < key[best])) best = p;
+    active[best] = 1;
+  }
+  free(key);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Camera and depth refinement (Section 3, Camera Refinement and Depth  */
 /* Refinement, Eqs. 4-5): f_i = f_i^0 (1 + gamma_i) scales both focal    */
 /* lengths of view i; each edge pixel's depth is Z^0 alpha + beta.       */
@@ -649,6 +690,8 @@ typedef struct {
   double delta, eps_z;
   int norm_mode;
   double lr_rot, lr_trans, beta1, beta2, eps;
+  int pair_budget;        /* M of Algorithm 3 (0 = every pair every step) */
+  uint64_t seed;          /* of the sub-sampling keys */
 } oracle_opt;
 
 /* lambda_s: linear from lambda0 to lambda1 over lambda_steps, then held. */
@@ -667,7 +710,13 @@ int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, cons
                     int64_t step0, int n_steps, double* m, double* v, double* loss_hist) {
   int n = S->n_views;
   double* G = (double*)malloc(sizeof(double) * 6 * n);
-  if (!G) return ORACLE_ENOMEM;
+  int P = S->n_pairs;
+  int* sub = (int*)malloc(sizeof(int) * 2 * (P > 0 ? P : 1));
+  uint8_t* act = (uint8_t*)malloc(P > 0 ? (size_t)P : 1);
+  if (!G || !sub || !act) {
+    free(G); free(sub); free(act);
+    return ORACLE_ENOMEM;
+  }
   oracle_params prm;
   prm.delta = o->delta;
   prm.eps_z = o->eps_z;
@@ -676,9 +725,24 @@ int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, cons
   for (int it = 0; it < n_steps; ++it) {
     int64_t s = step0 + it;
     prm.lambda = oracle_lambda(o, s);
+    /* Algorithm 3: the step's pairs, a fresh uniform subset when the budget is exceeded */
+    oracle_scene Ss = *S;
+    if (o->pair_budget > 0 && P > o->pair_budget) {
+      int rc0 = oracle_subsample(o->seed, s, P, o->pair_budget, act);
+      if (rc0) { free(G); free(sub); free(act); return rc0; }
+      int k = 0;
+      for (int p = 0; p < P; ++p)
+        if (act[p]) {
+          sub[2 * k] = S->pairs[2 * p];
+          sub[2 * k + 1] = S->pairs[2 * p + 1];
+          ++k;
+        }
+      Ss.pairs = sub;
+      Ss.n_pairs = k;
+    }
     double L;
-    int rc = oracle_loss_grad(S, T, &prm, &L, G, NULL, NULL, NULL, NULL, NULL);
-    if (rc) { free(G); return rc; }
+    int rc = oracle_loss_grad(&Ss, T, &prm, &L, G, NULL, NULL, NULL, NULL, NULL);
+    if (rc) { free(G); free(sub); free(act); return rc; }
     if (loss_hist) loss_hist[it] = L;
     double bc1 = 1.0 - pow(o->beta1, (double)(s + 1));
     double bc2 = 1.0 - pow(o->beta2, (double)(s + 1));
@@ -706,6 +770,6 @@ int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, cons
       memcpy(T + 12 * i, Tn, sizeof(Tn));
     }
   }
-  free(G);
+  free(G); free(sub); free(act);
   return ORACLE_OK;
 }
