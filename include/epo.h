@@ -117,6 +117,11 @@ typedef struct {
                                 lengths of view i; Eq. 5: every edge pixel's depth is
                                 Z^0 alpha + beta), set by epo_set_refinement and used by every
                                 evaluation and step; two records per thread */
+  int32_t pair_budget;       /* M of Algorithm 3 (Appendix A.3): when a scene has more
+                                pairs, every evaluation and step uses a fresh uniform random
+                                subset of M of them, drawn on the device from the step
+                                counter; 0 = every pair */
+  uint64_t subsample_seed;   /* seed of the subset draws (SplitMix64 keys of (seed, step, pair)) */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -124,7 +129,8 @@ typedef struct {
   int32_t n_scenes, n_views, n_pairs;
   int64_t n_records;         /* records kept on the device (all scenes) */
   int64_t n_dropped;         /* records dropped at creation (z <= 0 or non-finite) */
-  int64_t evals_per_step;    /* sum over pairs of |E_i| : edge-pixel x pair evaluations */
+  int64_t evals_per_step;    /* sum over pairs of |E_i| : edge-pixel x pair evaluations (with a
+                                pair budget: the expected number, min(1, M / P_s) of each pair's) */
   int64_t device_bytes;      /* library-owned device memory */
   int64_t record_bytes, map_bytes;
   int32_t n_tiles;           /* work items of the persistent kernels */
@@ -256,6 +262,10 @@ epo_status epo_set_refinement(epo_scene_t scene, const double* gamma, const floa
  * Host outputs; any gradient may be NULL.  Synchronises. */
 epo_status epo_refine_loss_and_grad(epo_scene_t scene, double* loss, double* grad, double* grad_gamma,
                                     float* grad_alpha, float* grad_beta);
+
+/* The pairs the most recent evaluation or step used (1) or skipped (0):
+ * n_pairs bytes (host).  Synchronises. */
+epo_status epo_get_pair_active(epo_scene_t scene, uint8_t* active);
 
 /* Evaluate only a subset of the pairs from now on (the stochastic viewgraph
  * sub-sampling of Algorithm 3 / Appendix A.3; the draw is the caller's).

@@ -39,6 +39,7 @@ EXPORTED = [
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
+    "epo_get_pair_active",
 ]
 
 
@@ -70,7 +71,8 @@ class epo_options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("gather", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32), ("tail_pairs", ctypes.c_int32),
-                ("refine", ctypes.c_int32)]
+                ("refine", ctypes.c_int32), ("pair_budget", ctypes.c_int32),
+                ("subsample_seed", ctypes.c_uint64)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -273,6 +275,13 @@ def epo_distance_field(edges_dev, W: int, H: int, map_dev, stream: int = 0):
 
 def epo_round_bf16(src_dev, dst_dev, n: int, stream: int = 0):
     check(load().epo_round_bf16(_ptr(src_dev), _ptr(dst_dev), ctypes.c_int64(n), ctypes.c_void_p(stream)))
+
+
+def epo_get_pair_active(scene, n_pairs: int):
+    import numpy as np
+    out = np.zeros(max(n_pairs, 1), dtype=np.uint8)
+    _call("epo_get_pair_active", scene, _ptr(out))
+    return out[:n_pairs].astype(bool)
 
 
 def epo_set_refinement(scene, gamma=None, alpha=None, beta=None):

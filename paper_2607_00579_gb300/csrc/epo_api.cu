@@ -112,6 +112,8 @@ struct epo_scene {
   int2* d_pair_ij = nullptr;
   double* d_pair_lw = nullptr;
   PoseEntry* d_pose_entries = nullptr;
+  // stochastic viewgraph sub-sampling (options.pair_budget)
+  int subsample = 0;  // 1 when some scene has more pairs than the budget
   // focal and depth refinement (options.refine)
   int refine = 0;
   double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
@@ -186,15 +188,13 @@ epo_status upload_weights(epo_scene* S, cudaStream_t st) {
     }
     lw[p] = w;
   }
-  std::vector<PoseEntry> ent((size_t)S->n_views * S->pose_stride, PoseEntry{-1, 0, 0.0});
+  std::vector<PoseEntry> ent((size_t)S->n_views * S->pose_stride, PoseEntry{-1, 0});
   for (int v = 0; v < S->n_views; ++v)
     for (int k = S->pose_off[v]; k < S->pose_off[v + 1]; ++k) {
       const int ref = S->pose_ref[k], p = ref >> 1;
       PoseEntry& e = ent[(size_t)v * S->pose_stride + (k - S->pose_off[v])];
-      if (lw[p] == 0.0) continue;
       e.p = p;
       e.scene_role = (S->pair_scene[p] << 1) | (ref & 1);
-      e.w = lw[p];
     }
   CK(cudaMemcpyAsync(S->d_pair_lw, lw.data(), lw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(S->d_pose_entries, ent.data(), ent.size() * sizeof(PoseEntry), cudaMemcpyHostToDevice, st));
@@ -245,6 +245,9 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.pair_lw = S->d_pair_lw;
   a.pose_entries = S->d_pose_entries;
   a.pose_stride = S->pose_stride;
+  a.pair_active_w = S->d_active;
+  a.pair_budget = S->opt.pair_budget;
+  a.subsample_seed = S->opt.subsample_seed;
   a.refine = S->refine;
   a.gamma = S->d_gamma;
   a.K64 = S->d_K64;
@@ -428,6 +431,7 @@ epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, int 
 epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval) {
   StepArgs a = step_args(S, T_eval, nullptr);
   MARK(0, s);
+  if (S->subsample) CK(launch_subsample(a, s));
   if (S->refine) CK(launch_refine_intrinsics(a, s));
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
@@ -443,6 +447,7 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   StepArgs a = step_args(S, S->d_T, nullptr);
   MARK(0, s);
+  if (S->subsample) CK(launch_subsample(a, s));
   if (S->refine) CK(launch_refine_intrinsics(a, s));
   CK(launch_pair_setup(a, MODE_FUSED, s));
   MARK(1, s);
@@ -502,6 +507,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
   if (o.tail_pairs < -1) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs must be -1, 0 or positive");
   if (o.refine != 0 && o.refine != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "refine must be 0 or 1");
+  if (o.pair_budget < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "pair_budget must be >= 0");
   if (o.refine && o.records_per_thread != 0 && o.records_per_thread != 2)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "refine scenes run two records per thread");
   S->refine = o.refine;
@@ -647,6 +653,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   }
   S->evals = 0;
   for (int p = 0; p < np; ++p) S->evals += S->views[S->pair_src[p]].n_rec;
+  for (int sc = 0; sc < n_scenes; ++sc)
+    if (o.pair_budget > 0 && S->scene_pair_off[sc + 1] - S->scene_pair_off[sc] > o.pair_budget) S->subsample = 1;
   // ---- device allocations (CK / ALLOC report into the handle under construction) ----
   {
     e = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
@@ -952,8 +960,20 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->n_records = S->n_records;
   info->n_dropped = S->n_dropped;
   int64_t ev = 0;
-  for (int p = 0; p < S->n_pairs; ++p)
-    if (S->active[p]) ev += S->views[S->pair_src[p]].n_rec;
+  if (S->subsample) {
+    // a random subset each step: the expected count, min(1, M / P_s) of every pair's records
+    double e = 0.0;
+    for (int sc = 0; sc < S->n_scenes; ++sc) {
+      const int P = S->scene_pair_off[sc + 1] - S->scene_pair_off[sc];
+      const double f = P > S->opt.pair_budget ? (double)S->opt.pair_budget / P : 1.0;
+      for (int p = S->scene_pair_off[sc]; p < S->scene_pair_off[sc + 1]; ++p)
+        e += f * (double)S->views[S->pair_src[p]].n_rec;
+    }
+    ev = (int64_t)llround(e);
+  } else {
+    for (int p = 0; p < S->n_pairs; ++p)
+      if (S->active[p]) ev += S->views[S->pair_src[p]].n_rec;
+  }
   info->evals_per_step = ev;
   info->device_bytes = S->device_bytes;
   info->record_bytes = S->n_records * (S->rec_dtype ? 8 : 16);
@@ -963,7 +983,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = S->refine ? 4 : 3;
+  info->kernels_per_step = 3 + S->refine + S->subsample;
   info->tail_pairs = S->tail;
   return EPO_OK;
 }
@@ -1062,6 +1082,7 @@ epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, nullptr);
   MARK(0, S->stream);
+  if (S->subsample) CK(launch_subsample(a, S->stream));
   if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
   CK(launch_pair_setup(a, MODE_FWD, S->stream));
   MARK(1, S->stream);
@@ -1079,6 +1100,7 @@ epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* d
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, dloss_dev);
   MARK(0, S->stream);
+  if (S->subsample) CK(launch_subsample(a, S->stream));
   if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
   CK(launch_pair_setup(a, MODE_BWD, S->stream));
   MARK(1, S->stream);
@@ -1194,6 +1216,7 @@ epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, d
   cudaStream_t s = S->stream;
   StepArgs a = step_args(S, S->d_T, nullptr);
   // forward: the loss and every pair's valid count (the pair means' denominators)
+  if (S->subsample) CK(launch_subsample(a, s));
   CK(launch_refine_intrinsics(a, s));
   CK(launch_pair_setup(a, MODE_FWD, s));
   st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, s);
@@ -1217,8 +1240,16 @@ epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, d
   return EPO_OK;
 }
 
+epo_status epo_get_pair_active(epo_scene_t S, uint8_t* active) {
+  if (!S || !active) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(active, S->d_active, (size_t)S->n_pairs, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
 epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
   if (!S || n < 0 || (n > 0 && !ids)) return fail(S, EPO_ERR_INVALID_ARG, "invalid subset");
+  if (S->opt.pair_budget > 0) return fail(S, EPO_ERR_INVALID_ARG, "the pairs are drawn on the device (pair_budget)");
   std::vector<uint8_t> act(S->n_pairs, n == 0 ? 1 : 0);
   for (int k = 0; k < n; ++k) {
     if (ids[k] < 0 || ids[k] >= S->n_pairs) return fail(S, EPO_ERR_INVALID_ARG, "pair id out of range");
@@ -1286,6 +1317,7 @@ epo_status epo_autotune(epo_scene_t S) {
       CK(launch_l2_read(flush, (int64_t)flush_bytes / 2, (unsigned*)((char*)flush + flush_bytes), S->sm_count,
                         S->stream));
     }
+    if (S->subsample) CK(launch_subsample(a, S->stream));
     if (S->refine) CK(launch_refine_intrinsics(a, S->stream));
     CK(launch_pair_setup(a, MODE_FUSED, S->stream));
     CK(cudaEventRecord(e0, S->stream));

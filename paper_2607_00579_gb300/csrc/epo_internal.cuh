@@ -107,13 +107,11 @@ struct EdgeArgs {
 };
 
 // One (pair, role) entry of a pose's gradient gather, laid out at a fixed stride per pose so
-// that the pose kernel reads it without an offset table.  w holds the pair's weight in the
-// scene's loss: 2 / (active pairs of the scene), times 1 / |E_i| under the Eq. 7
-// normaliser; p < 0 marks padding and inactive pairs.
+// that the pose kernel reads it without an offset table; p < 0 marks padding.  The pair's
+// weight in its scene's loss is pair_lw[p] (0 while the pair is not evaluated).
 struct PoseEntry {
   int32_t p;
   int32_t scene_role;  // scene << 1 | role (0 = target view j, 1 = source view i)
-  double w;
 };
 
 struct StepArgs {
@@ -157,7 +155,11 @@ struct StepArgs {
   const int32_t* loss_chunk_scene;   // n_loss_chunks
   double* loss_part;                 // n_loss_chunks partial sums of l_p
   const int2* loss_chunk_pairs;      // n_loss_chunks: [first, end) pairs of the chunk
-  const double* pair_lw;             // n_pairs: loss weight of the pair (PoseEntry::w), 0 if inactive
+  double* pair_lw;                   // n_pairs: the pair's weight in its scene's loss: 2 / (pairs the
+                                     // scene evaluates), times 1 / |E_i| under Eq. 7; 0 if not evaluated
+  uint8_t* pair_active_w;            // n_pairs: the same flags as pair_active, for the sub-sampling
+  int32_t pair_budget;               // M of Algorithm 3 (0 = every pair)
+  uint64_t subsample_seed;
   const PoseEntry* pose_entries;     // n_views x pose_stride
   int32_t pose_stride;
   unsigned int* scene_done;          // n_scenes completion counters of the loss chunks
@@ -174,6 +176,7 @@ struct StepArgs {
 // ---- launchers (epo_kernels.cu) ----
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
                                float* grad_beta, int64_t n, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);

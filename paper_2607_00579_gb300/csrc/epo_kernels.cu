@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         if (en.p < 0) continue;
         const int p = en.p;
         const double* acc = a.pair_acc + (size_t)kAcc * p;
-        double c = en.w;  // the pair's weight in its scene's loss
+        double c = a.pair_lw[p];  // the pair's weight in its scene's loss (0: not evaluated)
+        if (c == 0.0) continue;
         if (!a.norm_all) {
           const double n = acc[1];  // Algorithm 3: the pair's mean runs over its valid samples
           if (!(n > 0.0)) continue;
@@ -538,6 +539,122 @@ __global__ void k_round_bf16(const float* src, uint16_t* dst, int64_t n) {
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------
+// Stochastic viewgraph sub-sampling (Algorithm 3, Appendix A.3): each evaluation uses a
+// fresh uniform random subset of min(P_s, M) of a scene's P_s pairs.  Pair p (index within
+// its scene) at step s gets the key SplitMix64(seed ^ (s << 32 | p)) (the output function of
+// Steele, Lea and Flood's generator, OOPSLA 2014, on state + its golden-ratio increment);
+// the M smallest keys are taken, ties by index.  One block per scene finds the M-th
+// smallest key by a radix select over its 8 bytes (a 256-bin histogram per byte, high byte
+// first), then writes every pair's flag and loss weight.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t state) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t subsample_key(uint64_t seed, int64_t step, int p) {
+  return splitmix64_out(seed ^ (((uint64_t)step << 32) | (uint32_t)p));
+}
+
+constexpr int kSubsampleThreads = 1024;
+
+__global__ void __launch_bounds__(kSubsampleThreads) k_subsample(StepArgs a) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_k, s_eq;
+  const int sc = blockIdx.x;
+  const int off = a.scene_pair_off[sc], P = a.scene_pair_off[sc + 1] - off;
+  const int M = a.pair_budget;
+  const int64_t step = *a.step;
+  const uint64_t seed = a.subsample_seed;
+  const bool all = M <= 0 || P <= M;
+  const int na = all ? P : M;
+  uint64_t thr = ~0ull;
+  int k_eq = 0;
+  if (!all) {
+    if (threadIdx.x == 0) {
+      s_prefix = 0ull;
+      s_k = M;  // rank (1-based) of the cut within the keys that share the prefix
+    }
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+      __syncthreads();
+      const uint64_t prefix = s_prefix;
+      const uint64_t hm = shift == 56 ? 0ull : (~0ull << (shift + 8));
+      for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const uint64_t key = subsample_key(seed, step, p);
+        if ((key & hm) == (prefix & hm)) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned k = (unsigned)s_k;
+        unsigned cum = 0u;
+        int d = 0;
+        for (; d < 255; ++d) {
+          if (cum + hist[d] >= k) break;
+          cum += hist[d];
+        }
+        s_k = (int)(k - cum);
+        s_prefix = prefix | ((uint64_t)d << shift);
+      }
+      __syncthreads();
+    }
+    thr = s_prefix;  // the M-th smallest key
+    k_eq = s_k;      // how many of the keys equal to it are taken
+    if (threadIdx.x == 0) s_eq = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x)
+      if (subsample_key(seed, step, p) == thr) atomicAdd(&s_eq, 1);
+    __syncthreads();
+  }
+  const bool ties = !all && s_eq != k_eq;  // equal 64-bit keys across the cut: index order decides
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    bool act = true;
+    if (!all) {
+      const uint64_t key = subsample_key(seed, step, p);
+      act = key < thr || (key == thr && !ties);
+    }
+    const int q = off + p;
+    double w = 0.0;
+    if (act) {
+      w = 2.0 / na;
+      if (a.norm_all) {
+        const int32_t n = a.views[a.pair_src[q]].n_rec;
+        w = n > 0 ? w / (double)n : 0.0;
+      }
+    }
+    a.pair_active_w[q] = act ? 1 : 0;
+    a.pair_lw[q] = w;
+  }
+  __syncthreads();  // every flag is written before the tied ones are set in index order
+  if (ties && threadIdx.x == 0) {
+    int taken = 0;
+    for (int p = 0; p < P; ++p)
+      if (subsample_key(seed, step, p) == thr) {
+        const int q = off + p;
+        const bool act = taken++ < k_eq;
+        double w = 0.0;
+        if (act) {
+          w = 2.0 / na;
+          if (a.norm_all) {
+            const int32_t n = a.views[a.pair_src[q]].n_rec;
+            w = n > 0 ? w / (double)n : 0.0;
+          }
+        }
+        a.pair_active_w[q] = act ? 1 : 0;
+        a.pair_lw[q] = w;
+      }
+  }
+}
+
+cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s) {
+  k_subsample<<<a.n_scenes, kSubsampleThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s) {
   k_refine_intrinsics<<<std::max((a.n_views + 127) / 128, 1), 128, 0, s>>>(a);
   return cudaGetLastError();
