@@ -90,6 +90,14 @@ def _load():
         lib.oracle_pair_key.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32]
         lib.oracle_pair_key.restype = ctypes.c_uint64
         lib.oracle_subsample.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
+        lib.oracle_pose_change.argtypes = [P, P, ctypes.c_int, P, P]
+        lib.oracle_pose_change.restype = None
+        lib.oracle_percentile.argtypes = [P, ctypes.c_int, ctypes.c_double]
+        lib.oracle_percentile.restype = ctypes.c_double
+        lib.oracle_theta95.argtypes = [P, P, ctypes.c_int]
+        lib.oracle_theta95.restype = ctypes.c_double
+        lib.oracle_converge_update.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_int]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -261,6 +269,37 @@ def subsample(seed: int, step: int, n_pairs: int, M: int) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle_subsample failed ({rc})")
     return out[:n_pairs].astype(bool)
+
+
+def pose_change(T_prev, T_new):
+    """Per-view rotation and translation-direction change in degrees (Section 3)."""
+    A = np.ascontiguousarray(T_prev, dtype=np.float64).reshape(-1, 12)
+    Bn = np.ascontiguousarray(T_new, dtype=np.float64).reshape(-1, 12)
+    n = A.shape[0]
+    dR, dt = np.zeros(n), np.zeros(n)
+    _load().oracle_pose_change(_p(A), _p(Bn), n, _p(dR), _p(dt))
+    return dR, dt
+
+
+def percentile(x, q: float) -> float:
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_load().oracle_percentile(_p(a), a.size, q))
+
+
+def theta95(T_prev, T_new) -> float:
+    A = np.ascontiguousarray(T_prev, dtype=np.float64).reshape(-1, 12)
+    Bn = np.ascontiguousarray(T_new, dtype=np.float64).reshape(-1, 12)
+    return float(_load().oracle_theta95(_p(A), _p(Bn), A.shape[0]))
+
+
+def converge_run(thetas, eps1, w1, eps2, w2):
+    """Feeds a theta_95 sequence through the dual-phase schedule; returns the phase after
+    every step (1, 2; 3 = converged)."""
+    st = np.array([1, 0], dtype=np.int32)
+    out = []
+    for t in thetas:
+        out.append(int(_load().oracle_converge_update(_p(st), float(t), eps1, int(w1), eps2, int(w2))))
+    return out
 
 
 def set_threads(n: int = 0) -> int:

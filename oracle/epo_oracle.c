@@ -409,6 +409,92 @@ int oracle_subsample(uint64_t seed, int64_t step, int32_t n_pairs, int32_t M, ui
 }
 
 /* ------------------------------------------------------------------ */
+/* Optimization schedule (Section 3): per-view pose change in degrees,  */
+/* its 95th percentile over the poses, and the dual-phase convergence.  */
+/* ------------------------------------------------------------------ */
+/* Rotation change: the angle of R_new R_prev^T, 180/pi arccos((tr - 1) / 2); translation
+ * change: the angle between t_new and t_prev, 180/pi arccos(t_new . t_prev / (|t_new| |t_prev|))
+ * (0 when either is the zero vector).  The arccos arguments are clipped to [-1, 1]. */
+void oracle_pose_change(const double* T_prev, const double* T_new, int n, double* dR, double* dt) {
+  const double deg = 180.0 / 3.14159265358979323846;
+  for (int v = 0; v < n; ++v) {
+    const double* A = T_new + 12 * v;
+    const double* B = T_prev + 12 * v;
+    double tr = 0.0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) tr += A[4 * r + c] * B[4 * r + c];
+    double cr = (tr - 1.0) / 2.0;
+    if (cr > 1.0) cr = 1.0;
+    if (cr < -1.0) cr = -1.0;
+    dR[v] = deg * acos(cr);
+    double na = sqrt(A[3] * A[3] + A[7] * A[7] + A[11] * A[11]);
+    double nb = sqrt(B[3] * B[3] + B[7] * B[7] + B[11] * B[11]);
+    if (na == 0.0 || nb == 0.0) {
+      dt[v] = 0.0;
+      continue;
+    }
+    double ct = (A[3] * B[3] + A[7] * B[7] + A[11] * B[11]) / (na * nb);
+    if (ct > 1.0) ct = 1.0;
+    if (ct < -1.0) ct = -1.0;
+    dt[v] = deg * acos(ct);
+  }
+}
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* q-th percentile (0..100) with linear interpolation between the closest order statistics
+ * (the default of the common numerical libraries). */
+double oracle_percentile(const double* x, int n, double q) {
+  if (n <= 0) return 0.0;
+  double* s = (double*)malloc(sizeof(double) * n);
+  if (!s) return NAN;
+  memcpy(s, x, sizeof(double) * n);
+  qsort(s, n, sizeof(double), cmp_double);
+  double pos = q / 100.0 * (n - 1);
+  int lo = (int)floor(pos);
+  if (lo >= n - 1) {
+    double r = s[n - 1];
+    free(s);
+    return r;
+  }
+  double r = s[lo] + (s[lo + 1] - s[lo]) * (pos - lo);
+  free(s);
+  return r;
+}
+
+/* theta_95 = max(95th percentile of dR, 95th percentile of dt) over the n poses. */
+double oracle_theta95(const double* T_prev, const double* T_new, int n) {
+  double* dR = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double* dt = (double*)malloc(sizeof(double) * (n > 0 ? n : 1));
+  if (!dR || !dt) { free(dR); free(dt); return NAN; }
+  oracle_pose_change(T_prev, T_new, n, dR, dt);
+  double a = oracle_percentile(dR, n, 95.0), b = oracle_percentile(dt, n, 95.0);
+  free(dR); free(dt);
+  return a > b ? a : b;
+}
+
+/* One step of the dual-phase schedule.  state[0]: phase (1, 2; 3 = converged),
+ * state[1]: consecutive steps below the current phase's threshold.  Phase 1 ends (depth
+ * optimisation starts) after w1 consecutive steps with theta < eps1; phase 2 ends (the run
+ * stops) after w2 consecutive steps with theta < eps2.  Returns the new phase. */
+int oracle_converge_update(int32_t* state, double theta, double eps1, int w1, double eps2, int w2) {
+  if (state[0] == 1) {
+    state[1] = theta < eps1 ? state[1] + 1 : 0;
+    if (state[1] >= w1) {
+      state[0] = 2;
+      state[1] = 0;
+    }
+  } else if (state[0] == 2) {
+    state[1] = theta < eps2 ? state[1] + 1 : 0;
+    if (state[1] >= w2) state[0] = 3;
+  }
+  return state[0];
+}
+
+/* ------------------------------------------------------------------ */
 /* Camera and depth refinement (Section 3, Camera Refinement and Depth  */
 /* Refinement, Eqs. 4-5): f_i = f_i^0 (1 + gamma_i) scales both focal    */
 /* lengths of view i; each edge pixel's depth is Z^0 alpha + beta.       */
