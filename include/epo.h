@@ -122,6 +122,13 @@ typedef struct {
                                 subset of M of them, drawn on the device from the step
                                 counter; 0 = every pair */
   uint64_t subsample_seed;   /* seed of the subset draws (SplitMix64 keys of (seed, step, pair)) */
+  double sched_eps1, sched_eps2; /* Optimization Schedule (Section 3): thresholds in degrees */
+  int32_t schedule;          /* 1: after every step, theta_95 = max of the 95th percentiles over
+                                the scene's poses of the rotation and translation-direction
+                                changes; phase 1 ends after sched_w1 consecutive steps with
+                                theta_95 < sched_eps1, phase 2 (the run) after sched_w2 steps
+                                below sched_eps2, and a converged scene's poses stop changing */
+  int32_t sched_w1, sched_w2; /* window sizes (defaults: the paper's 25 / 50 and 0.5 / 0.1) */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -262,6 +269,14 @@ epo_status epo_set_refinement(epo_scene_t scene, const double* gamma, const floa
  * Host outputs; any gradient may be NULL.  Synchronises. */
 epo_status epo_refine_loss_and_grad(epo_scene_t scene, double* loss, double* grad, double* grad_gamma,
                                     float* grad_alpha, float* grad_beta);
+
+/* State of the optimisation schedule per scene (options.schedule): theta95
+ * (n_scenes doubles, of the most recent step), phase (n_scenes: 1, 2, 3 =
+ * converged), switch_step and stop_step (n_scenes each: the step at which
+ * phase 2 began / the run converged, -1 if not yet).  Host outputs, any may be
+ * NULL.  Synchronises. */
+epo_status epo_get_schedule(epo_scene_t scene, double* theta95, int32_t* phase, int64_t* switch_step,
+                            int64_t* stop_step);
 
 /* The pairs the most recent evaluation or step used (1) or skipped (0):
  * n_pairs bytes (host).  Synchronises. */

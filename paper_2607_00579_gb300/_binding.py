@@ -39,7 +39,7 @@ EXPORTED = [
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
-    "epo_get_pair_active",
+    "epo_get_pair_active", "epo_get_schedule",
 ]
 
 
@@ -72,7 +72,9 @@ class epo_options(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("records_per_thread", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("timing", ctypes.c_int32), ("tail_pairs", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("pair_budget", ctypes.c_int32),
-                ("subsample_seed", ctypes.c_uint64)]
+                ("subsample_seed", ctypes.c_uint64), ("sched_eps1", ctypes.c_double),
+                ("sched_eps2", ctypes.c_double), ("schedule", ctypes.c_int32), ("sched_w1", ctypes.c_int32),
+                ("sched_w2", ctypes.c_int32)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -275,6 +277,17 @@ def epo_distance_field(edges_dev, W: int, H: int, map_dev, stream: int = 0):
 
 def epo_round_bf16(src_dev, dst_dev, n: int, stream: int = 0):
     check(load().epo_round_bf16(_ptr(src_dev), _ptr(dst_dev), ctypes.c_int64(n), ctypes.c_void_p(stream)))
+
+
+def epo_get_schedule(scene, n_scenes: int):
+    """Returns (theta95, phase, switch_step, stop_step), one entry per scene."""
+    import numpy as np
+    th = np.zeros(n_scenes)
+    ph = np.zeros(n_scenes, dtype=np.int32)
+    sw = np.zeros(n_scenes, dtype=np.int64)
+    st = np.zeros(n_scenes, dtype=np.int64)
+    _call("epo_get_schedule", scene, _ptr(th), _ptr(ph), _ptr(sw), _ptr(st))
+    return th, ph, sw, st
 
 
 def epo_get_pair_active(scene, n_pairs: int):

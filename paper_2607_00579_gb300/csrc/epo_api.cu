@@ -114,6 +114,11 @@ struct epo_scene {
   PoseEntry* d_pose_entries = nullptr;
   // stochastic viewgraph sub-sampling (options.pair_budget)
   int subsample = 0;  // 1 when some scene has more pairs than the budget
+  // optimisation schedule (options.schedule)
+  int32_t* d_scene_view_off = nullptr;
+  double *d_pose_dR = nullptr, *d_pose_dt = nullptr, *d_theta95 = nullptr;
+  int32_t* d_sched_state = nullptr;
+  int64_t* d_sched_steps = nullptr;
   // focal and depth refinement (options.refine)
   int refine = 0;
   double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
@@ -248,6 +253,17 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.pair_active_w = S->d_active;
   a.pair_budget = S->opt.pair_budget;
   a.subsample_seed = S->opt.subsample_seed;
+  a.schedule = S->opt.schedule;
+  a.scene_view_off = S->d_scene_view_off;
+  a.pose_dR = S->d_pose_dR;
+  a.pose_dt = S->d_pose_dt;
+  a.sched_state = S->d_sched_state;
+  a.theta95 = S->d_theta95;
+  a.sched_steps = S->d_sched_steps;
+  a.sched_eps1 = S->opt.sched_eps1;
+  a.sched_eps2 = S->opt.sched_eps2;
+  a.sched_w1 = S->opt.sched_w1;
+  a.sched_w2 = S->opt.sched_w2;
   a.refine = S->refine;
   a.gamma = S->d_gamma;
   a.K64 = S->d_K64;
@@ -454,6 +470,7 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 2, s));
+  if (S->opt.schedule) CK(launch_schedule(a, s));
   MARK(3, s);
   return EPO_OK;
 }
@@ -508,6 +525,9 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   if (o.tail_pairs < -1) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs must be -1, 0 or positive");
   if (o.refine != 0 && o.refine != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "refine must be 0 or 1");
   if (o.pair_budget < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "pair_budget must be >= 0");
+  if (o.schedule != 0 && o.schedule != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "schedule must be 0 or 1");
+  if (o.schedule && (o.sched_w1 < 1 || o.sched_w2 < 1 || !(o.sched_eps1 >= 0) || !(o.sched_eps2 >= 0)))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "schedule windows must be >= 1 and thresholds >= 0");
   if (o.refine && o.records_per_thread != 0 && o.records_per_thread != 2)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "refine scenes run two records per thread");
   S->refine = o.refine;
@@ -724,6 +744,28 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_pair_ij, np);
     ALLOC(S->d_pair_lw, np);
     ALLOC(S->d_pose_entries, (size_t)nv * S->pose_stride);
+    if (o.schedule) {
+      ALLOC(S->d_scene_view_off, n_scenes + 1);
+      ALLOC(S->d_pose_dR, nv);
+      ALLOC(S->d_pose_dt, nv);
+      ALLOC(S->d_sched_state, 2 * (size_t)n_scenes);
+      ALLOC(S->d_theta95, n_scenes);
+      ALLOC(S->d_sched_steps, 2 * (size_t)n_scenes);
+      std::vector<int32_t> vo(1, 0), ss(2 * (size_t)n_scenes);
+      for (int sc = 0; sc < n_scenes; ++sc) {
+        vo.push_back(vo.back() + descs[sc].n_views);
+        ss[2 * sc] = 1;
+        ss[2 * sc + 1] = 0;
+      }
+      std::vector<int64_t> steps(2 * (size_t)n_scenes, -1);
+      std::vector<double> th(n_scenes, 0.0);
+      CK(cudaMemcpy(S->d_scene_view_off, vo.data(), vo.size() * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(S->d_sched_state, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(S->d_sched_steps, steps.data(), steps.size() * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(S->d_theta95, th.data(), th.size() * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemset(S->d_pose_dR, 0, (size_t)nv * 8));
+      CK(cudaMemset(S->d_pose_dt, 0, (size_t)nv * 8));
+    }
     if (S->refine) {
       ALLOC(S->d_gamma, nv);
       ALLOC(S->d_K64r, (size_t)6 * nv);
@@ -922,6 +964,10 @@ void epo_default_options(epo_options* o) {
   o->autotune = 0;
   o->gather = EPO_GATHER_AUTO;
   o->tail_pairs = -1;
+  o->sched_eps1 = 0.5;  // degrees; the paper's windows and tolerances
+  o->sched_eps2 = 0.1;
+  o->sched_w1 = 25;
+  o->sched_w2 = 50;
 }
 
 int32_t epo_abi_version(void) { return EPO_ABI_VERSION; }
@@ -983,7 +1029,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = 3 + S->refine + S->subsample;
+  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule;
   info->tail_pairs = S->tail;
   return EPO_OK;
 }
@@ -1237,6 +1283,25 @@ epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, d
   if (grad_beta && S->n_records)
     CK(cudaMemcpyAsync(grad_beta, S->d_grad_beta, (size_t)S->n_records * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return EPO_OK;
+}
+
+epo_status epo_get_schedule(epo_scene_t S, double* theta95, int32_t* phase, int64_t* switch_step,
+                            int64_t* stop_step) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (!S->opt.schedule) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.schedule = 1");
+  const int ns = S->n_scenes;
+  std::vector<int32_t> st(2 * (size_t)ns);
+  std::vector<int64_t> steps(2 * (size_t)ns);
+  CK(cudaMemcpyAsync(st.data(), S->d_sched_state, st.size() * 4, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaMemcpyAsync(steps.data(), S->d_sched_steps, steps.size() * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (theta95) CK(cudaMemcpyAsync(theta95, S->d_theta95, (size_t)ns * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  for (int sc = 0; sc < ns; ++sc) {
+    if (phase) phase[sc] = st[2 * sc];
+    if (switch_step) switch_step[sc] = steps[2 * sc];
+    if (stop_step) stop_step[sc] = steps[2 * sc + 1];
+  }
   return EPO_OK;
 }
 

@@ -160,6 +160,16 @@ struct StepArgs {
   uint8_t* pair_active_w;            // n_pairs: the same flags as pair_active, for the sub-sampling
   int32_t pair_budget;               // M of Algorithm 3 (0 = every pair)
   uint64_t subsample_seed;
+  // optimisation schedule (Section 3): per-view changes of the step, per-scene state
+  int32_t schedule;
+  const int32_t* scene_view_off;     // n_scenes + 1
+  double* pose_dR;                   // n_views: rotation change of the step, degrees
+  double* pose_dt;                   // n_views: translation-direction change, degrees
+  int32_t* sched_state;              // n_scenes x 2: phase (1, 2, 3 = converged), consecutive steps
+  double* theta95;                   // n_scenes
+  int64_t* sched_steps;              // n_scenes x 2: step of the switch to phase 2, of convergence
+  double sched_eps1, sched_eps2;
+  int32_t sched_w1, sched_w2;
   const PoseEntry* pose_entries;     // n_views x pose_stride
   int32_t pose_stride;
   unsigned int* scene_done;          // n_scenes completion counters of the loss chunks
@@ -177,6 +187,7 @@ struct StepArgs {
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_schedule(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
                                float* grad_beta, int64_t n, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);

@@ -171,6 +171,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       bp0 = a.bpow[0];
       bp1 = a.bpow[1];
     }
+    // a scene whose schedule has converged keeps its poses
+    const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
     double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double gg = 0.0;  // refine scenes: dL/dgamma_v, before the 1 / (1 + gamma_v) factor
     if (vv) {
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     if (with_grad == 2) {
       const bool bad = vv && e < 6 && !isfinite(G);
       const unsigned badmask = __ballot_sync(0xffffffffu, bad);
-      const bool skip = !vv || (flag0 & 1) || a.fixed[v] || ((badmask >> base) & 0xffffu);
+      const bool skip = !vv || (flag0 & 1) || a.fixed[v] || conv || ((badmask >> base) & 0xffffu);
       double xi = 0.0;
       if (!skip && e < 6) {
         const size_t o = 6 * (size_t)v + e;
@@ -288,6 +290,31 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       if (!skip && e < 12) Tnew = fma(E0, Tc0, fma(E1, Tc1, fma(E2, Tc2, c == 3 ? E3 : 0.0)));
       __syncwarp();  // every lane has read the old pose before any lane writes it
       if (!skip && e < 12) a.T_store[12 * (size_t)v + e] = Tnew;
+      if (a.schedule) {
+        // the step's pose change (Section 3, Optimization Schedule): lane (r, c) holds entry
+        // (r, c) of the old and the new pose; tr(R_new R_old^T) and the translations' dot
+        // product and norms are reduced over the pose's 16 lanes in a fixed order
+        const double Told = r == 0 ? Tc0 : (r == 1 ? Tc1 : Tc2);
+        const double Tn = skip ? Told : Tnew;
+        double tr = (e < 12 && c < 3) ? Tn * Told : 0.0;
+        double dot = (e < 12 && c == 3) ? Tn * Told : 0.0;
+        double nn = (e < 12 && c == 3) ? Tn * Tn : 0.0;
+        double no = (e < 12 && c == 3) ? Told * Told : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          tr += __shfl_xor_sync(0xffffffffu, tr, o);
+          dot += __shfl_xor_sync(0xffffffffu, dot, o);
+          nn += __shfl_xor_sync(0xffffffffu, nn, o);
+          no += __shfl_xor_sync(0xffffffffu, no, o);
+        }
+        if (vv && e == 0) {
+          const double deg = 180.0 / 3.14159265358979323846;
+          const double cr = fmin(1.0, fmax(-1.0, (tr - 1.0) * 0.5));
+          a.pose_dR[v] = deg * acos(cr);
+          const double nm = sqrt(nn) * sqrt(no);
+          a.pose_dt[v] = nm > 0.0 ? deg * acos(fmin(1.0, fmax(-1.0, dot / nm))) : 0.0;
+        }
+      }
     }
   } else {
     // per-scene loss (Eq. 6): this block sums l_p over kLossChunk consecutive pairs of one
@@ -648,6 +675,93 @@ __global__ void __launch_bounds__(kSubsampleThreads) k_subsample(StepArgs a) {
         a.pair_lw[q] = w;
       }
   }
+}
+
+// ------------------------------------------------------------------------------------
+// Optimization schedule (Section 3): after every step, theta_95 = max(95th percentile of
+// the rotation changes, 95th percentile of the translation-direction changes) over the
+// scene's poses, then the dual-phase rule.  One block per scene; the percentile takes the
+// two order statistics around 0.95 (n - 1) by radix select over the bit patterns of the
+// (non-negative) doubles and interpolates between them linearly.
+// ------------------------------------------------------------------------------------
+constexpr int kScheduleThreads = 256;
+
+// k-th smallest (0-based) of n non-negative doubles; every thread of the block calls it.
+__device__ double block_kth(const double* x, int n, int k, unsigned* hist, unsigned long long* s_prefix, int* s_k) {
+  if (threadIdx.x == 0) {
+    *s_prefix = 0ull;
+    *s_k = k + 1;
+  }
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    const unsigned long long prefix = *s_prefix;
+    const unsigned long long hm = shift == 56 ? 0ull : (~0ull << (shift + 8));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned long long key = (unsigned long long)__double_as_longlong(x[i]);
+      if ((key & hm) == (prefix & hm)) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned kk = (unsigned)*s_k;
+      unsigned cum = 0u;
+      int d = 0;
+      for (; d < 255; ++d) {
+        if (cum + hist[d] >= kk) break;
+        cum += hist[d];
+      }
+      *s_k = (int)(kk - cum);
+      *s_prefix = prefix | ((unsigned long long)d << shift);
+    }
+    __syncthreads();
+  }
+  return __longlong_as_double((long long)*s_prefix);
+}
+
+__device__ double block_percentile95(const double* x, int n, unsigned* hist, unsigned long long* s_prefix, int* s_k) {
+  if (n <= 0) return 0.0;
+  const double pos = 0.95 * (double)(n - 1);
+  const int lo = (int)floor(pos);
+  const double a = block_kth(x, n, lo, hist, s_prefix, s_k);
+  if (lo >= n - 1) return a;
+  const double b = block_kth(x, n, lo + 1, hist, s_prefix, s_k);
+  return a + (b - a) * (pos - (double)lo);
+}
+
+__global__ void __launch_bounds__(kScheduleThreads) k_schedule(StepArgs a) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_k;
+  const int sc = blockIdx.x;
+  const int v0 = a.scene_view_off[sc], n = a.scene_view_off[sc + 1] - v0;
+  int32_t* st = a.sched_state + 2 * sc;
+  if (st[0] == 3) return;  // uniform over the block: converged earlier
+  const double pR = block_percentile95(a.pose_dR + v0, n, hist, &s_prefix, &s_k);
+  const double pT = block_percentile95(a.pose_dt + v0, n, hist, &s_prefix, &s_k);
+  if (threadIdx.x == 0) {
+    const double theta = fmax(pR, pT);
+    a.theta95[sc] = theta;
+    const int64_t step = *a.step - 1;  // the step just taken (the pose kernel advanced the counter)
+    if (st[0] == 1) {
+      st[1] = theta < a.sched_eps1 ? st[1] + 1 : 0;
+      if (st[1] >= a.sched_w1) {
+        st[0] = 2;
+        st[1] = 0;
+        a.sched_steps[2 * sc] = step;
+      }
+    } else if (st[0] == 2) {
+      st[1] = theta < a.sched_eps2 ? st[1] + 1 : 0;
+      if (st[1] >= a.sched_w2) {
+        st[0] = 3;
+        a.sched_steps[2 * sc + 1] = step;
+      }
+    }
+  }
+}
+
+cudaError_t launch_schedule(const StepArgs& a, cudaStream_t s) {
+  k_schedule<<<a.n_scenes, kScheduleThreads, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s) {
