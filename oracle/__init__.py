@@ -98,6 +98,7 @@ def _load():
         lib.oracle_theta95.restype = ctypes.c_double
         lib.oracle_converge_update.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_int]
+        lib.oracle_viewgraph.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, ctypes.c_double, P]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -300,6 +301,30 @@ def converge_run(thetas, eps1, w1, eps2, w2):
     for t in thetas:
         out.append(int(_load().oracle_converge_update(_p(st), float(t), eps1, int(w1), eps2, int(w2))))
     return out
+
+
+def viewgraph(W, H, K, T, depths, stride: int = 4, tau: float = 3.0) -> np.ndarray:
+    """Round-trip-consistent fraction f[i, j] of view i's grid pixels (Section 3, Viewgraph
+    Estimation): n x n, zero diagonal.  depths: per-view (H, W) float maps."""
+    n = len(W)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    Ka = np.ascontiguousarray(K, dtype=np.float64).reshape(n, 4)
+    Ta = np.ascontiguousarray(T, dtype=np.float64).reshape(n, 12)
+    Z = np.ascontiguousarray(np.concatenate([np.asarray(d, np.float32).ravel() for d in depths]))
+    f = np.zeros((n, n))
+    rc = _load().oracle_viewgraph(n, _p(Wa), _p(Ha), _p(Ka), _p(Ta), _p(Z), stride, tau, _p(f))
+    if rc:
+        raise ValueError(f"oracle_viewgraph failed ({rc})")
+    return f
+
+
+def viewgraph_pairs(frac: np.ndarray, min_frac: float = 0.125) -> np.ndarray:
+    """Directed pairs (i, j) of the undirected pairs whose round-trip fraction is at least
+    min_frac in both directions, in row-major order."""
+    keep = np.minimum(frac, frac.T) >= min_frac
+    np.fill_diagonal(keep, False)
+    return np.argwhere(keep).astype(np.int32)
 
 
 def set_threads(n: int = 0) -> int:

@@ -409,6 +409,79 @@ int oracle_subsample(uint64_t seed, int64_t step, int32_t n_pairs, int32_t M, ui
 }
 
 /* ------------------------------------------------------------------ */
+/* Viewgraph estimation (Section 3, Eq. 2; Algorithm 1 BuildViewgraph):   */
+/* the fraction of grid pixels of view i that survive the round trip     */
+/* i -> j -> i within tau pixels.                                        */
+/* ------------------------------------------------------------------ */
+/* Depth of view v at the pixel nearest to (x, y); 0 when outside the image. */
+static double depth_nearest(const float* Z, int W, int H, double x, double y) {
+  int xi = (int)floor(x + 0.5), yi = (int)floor(y + 0.5);
+  if (xi < 0 || xi >= W || yi < 0 || yi >= H) return 0.0;
+  return (double)Z[(int64_t)yi * W + xi];
+}
+
+/* camera v pixel (x, y) at depth z -> camera w pixel; returns 0 when not in front. */
+static int reproject(const double* Kv, const double* Tv, const double* Kw, const double* Tw, double x, double y,
+                     double z, double* xo, double* yo) {
+  double Xc[3] = {(x - Kv[2]) / Kv[0] * z, (y - Kv[3]) / Kv[1] * z, z};
+  double q[3] = {Xc[0] - Tv[3], Xc[1] - Tv[7], Xc[2] - Tv[11]};
+  double Xw[3];
+  for (int c = 0; c < 3; ++c) Xw[c] = Tv[c] * q[0] + Tv[4 + c] * q[1] + Tv[8 + c] * q[2];
+  double Y[3];
+  for (int r = 0; r < 3; ++r) Y[r] = Tw[4 * r] * Xw[0] + Tw[4 * r + 1] * Xw[1] + Tw[4 * r + 2] * Xw[2] + Tw[4 * r + 3];
+  if (!(Y[2] > 0.0)) return 0;
+  *xo = Kw[0] * Y[0] / Y[2] + Kw[2];
+  *yo = Kw[1] * Y[1] / Y[2] + Kw[3];
+  return 1;
+}
+
+/*
+ * For every ordered pair (i, j), i != j: over the source pixels (x, y) = (a g, b g) of view i
+ * whose depth is positive and finite, the fraction whose round trip
+ *   p -> p_{i->j} (with Z_i at p) -> p_{i->j->i} (with Z_j at the pixel nearest p_{i->j})
+ * stays in front of both cameras, inside view j, and returns within tau pixels of p.
+ * depth: the views' W x H maps concatenated (row-major, float).  frac: n x n (diagonal 0).
+ */
+int oracle_viewgraph(int n, const int* W, const int* H, const double* K, const double* T, const float* depth,
+                     int stride, double tau, double* frac) {
+  if (n < 1 || stride < 1 || !W || !H || !K || !T || !depth || !frac) return ORACLE_EINVAL;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+  if (!off) return ORACLE_ENOMEM;
+  off[0] = 0;
+  for (int v = 0; v < n; ++v) off[v + 1] = off[v] + (int64_t)W[v] * H[v];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < n; ++i) {
+    const float* Zi = depth + off[i];
+    for (int j = 0; j < n; ++j) {
+      if (i == j) {
+        frac[(int64_t)i * n + j] = 0.0;
+        continue;
+      }
+      const float* Zj = depth + off[j];
+      int64_t valid = 0, good = 0;
+      for (int y = 0; y < H[i]; y += stride)
+        for (int x = 0; x < W[i]; x += stride) {
+          double z = (double)Zi[(int64_t)y * W[i] + x];
+          if (!(z > 0.0) || !isfinite(z)) continue;
+          ++valid;
+          double xj, yj;
+          if (!reproject(K + 4 * i, T + 12 * i, K + 4 * j, T + 12 * j, x, y, z, &xj, &yj)) continue;
+          if (!(xj >= 0.0 && xj <= W[j] - 1 && yj >= 0.0 && yj <= H[j] - 1)) continue;
+          double zj = depth_nearest(Zj, W[j], H[j], xj, yj);
+          if (!(zj > 0.0) || !isfinite(zj)) continue;
+          double xb, yb;
+          if (!reproject(K + 4 * j, T + 12 * j, K + 4 * i, T + 12 * i, xj, yj, zj, &xb, &yb)) continue;
+          double dx = xb - x, dy = yb - y;
+          if (sqrt(dx * dx + dy * dy) < tau) ++good;
+        }
+      frac[(int64_t)i * n + j] = valid > 0 ? (double)good / (double)valid : 0.0;
+    }
+  }
+  free(off);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Optimization schedule (Section 3): per-view pose change in degrees,  */
 /* its 95th percentile over the poses, and the dual-phase convergence.  */
 /* ------------------------------------------------------------------ */
