@@ -74,7 +74,7 @@ class Workload:
         self.key = key
         self.name = WORKLOADS[key]
         if key == "ring32":
-            self.scenes = [synth.make_scene(synth.RING32_518x392)]
+            self.scenes = [synth.make_scene(synth.RING32_518x392, keep_depth=True)]
         elif key == "walk200":
             self.scenes = [synth.make_scene(synth.WALK200_518x392)]
         elif key == "batch64":
@@ -489,6 +489,7 @@ def run_ours(args):
         line["fp32_form"] = fp32_form_leg(epo, torch, wl, s, scene, lr, evals, args, flush_l2, stream)
     elif wl.key == "ring32":
         line["refine"] = refine_leg(epo, torch, wl, parts, (rd, md), lr, evals, args, flush_l2)
+        line["viewgraph"] = viewgraph_leg(epo, torch, wl)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -526,6 +527,27 @@ def gather_roofline(epo, wl, info, evals, kern_ms, hbm_peak):
 
 
 ACC_STEPS = 100  # optimisation steps behind the final-accuracy comparisons
+
+
+def viewgraph_leg(epo, torch, wl, stride=4):
+    """Viewgraph estimation (Section 3, Eq. 2): every ordered pair's round-trip fraction over
+    a grid of source pixels, on the GPU in FP64, at the initial poses and depths."""
+    sc = wl.scenes[0]
+    depth = torch.cat([torch.from_numpy(d).reshape(-1) for d in sc.depth]).cuda()
+    run = lambda: epo.build_viewgraph(sc.W, sc.H, sc.K, sc.T_init, depth, stride=stride, tau=3.0, min_frac=0.125)
+    run()
+    n = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        frac, pairs = run()
+    ms = 1e3 * (time.perf_counter() - t0) / n
+    grid = sum(((int(w) + stride - 1) // stride) * ((int(h) + stride - 1) // stride) for w, h in zip(sc.W, sc.H))
+    trips = grid * (sc.n_views - 1)
+    return {"ms": ms, "round_trips": trips, "round_trips_per_s": trips / (ms * 1e-3), "grid_stride": stride,
+            "tau_px": 3.0, "min_frac": 0.125, "pairs_kept": int(len(pairs)),
+            "pairs_candidate": sc.n_views * (sc.n_views - 1),
+            "note": "wall time of epo_build_viewgraph (FP64 round trips, host copy of the fraction matrix)"}
 
 
 def refine_leg(epo, torch, wl, parts, dtypes, lr, evals, args, flush_l2):

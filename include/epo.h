@@ -304,6 +304,24 @@ epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, fl
 /* Round n floats to bfloat16 (round to nearest even), device buffers. */
 epo_status epo_round_bf16(const float* src_dev, uint16_t* dst_dev, int64_t n, void* cuda_stream);
 
+/* Viewgraph estimation (Section 3, Viewgraph Estimation, Eq. 2; Algorithm 1
+ * BuildViewgraph), run once before the optimisation.  For every ordered pair
+ * (i, j) of the n_views views: over the grid pixels (a stride, b stride) of
+ * view i with a positive finite depth, the fraction whose round trip i -> j
+ * -> i (projected with Z_i, lifted in j with Z_j at the nearest pixel,
+ * projected back) stays in front of both cameras and inside view j and
+ * returns within tau pixels.  W, H: n_views each; K: n_views x 4 (fx, fy, cx,
+ * cy); T: n_views x 12 world -> camera [R|t] (host, FP64); depth_dev: the
+ * views' W x H float depth maps concatenated (device, row-major).  Outputs
+ * (host): frac n_views x n_views (may be NULL; diagonal 0), pairs 2 x
+ * n_views (n_views - 1) int32 capacity (may be NULL): the directed pairs of
+ * the undirected pairs whose fraction is >= min_frac both ways, row-major;
+ * *n_pairs their count.  FP64 on the device; synchronises.  Invalid sizes or
+ * intrinsics: EPO_ERR_INVALID_ARG; allocation failure: EPO_ERR_OOM. */
+epo_status epo_build_viewgraph(int32_t n_views, const int32_t* W, const int32_t* H, const double* K, const double* T,
+                               const float* depth_dev, int32_t stride, double tau, double min_frac, double* frac,
+                               int32_t* pairs, int32_t* n_pairs, void* cuda_stream);
+
 /* Gather-throughput probe for the roofline of the sampling step (Eq. 8's
  * bilinear sample; the paper names projection and sampling as the dominant
  * cost, Section 5 / Appendix A): 2x2 footprints per second that this GPU

@@ -202,6 +202,18 @@ def distance_field(edges, stream: Optional[int] = None):
     return out
 
 
+def build_viewgraph(W, H, K, T, depths, stride: int = 4, tau: float = 3.0, min_frac: float = 0.125,
+                    stream: Optional[int] = None):
+    """Viewgraph estimation on the GPU (Section 3): returns (frac (n, n), pairs (m, 2)) for
+    per-view depth maps given as CUDA float tensors (H, W) or one concatenated tensor."""
+    import torch
+    if isinstance(depths, (list, tuple)):
+        depths = torch.cat([d.reshape(-1).float() for d in depths])
+    depths = depths.contiguous()
+    return B.epo_build_viewgraph(W, H, K, T, depths, stride, tau, min_frac,
+                                 _current_stream() if stream is None else stream)
+
+
 def round_bf16(x, stream: Optional[int] = None):
     """float32 CUDA tensor -> the bfloat16 bits (int16 tensor of the same shape), RNE."""
     import torch

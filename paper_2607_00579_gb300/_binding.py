@@ -39,7 +39,7 @@ EXPORTED = [
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
-    "epo_get_pair_active", "epo_get_schedule",
+    "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph",
 ]
 
 
@@ -316,6 +316,23 @@ def epo_refine_loss_and_grad(scene, n_scenes: int, n_views: int, n_records: int)
     gb = np.zeros(max(n_records, 1), dtype=np.float32)
     _call("epo_refine_loss_and_grad", scene, _ptr(loss), _ptr(grad), _ptr(gg), _ptr(ga), _ptr(gb))
     return loss, grad, gg, ga[:n_records], gb[:n_records]
+
+
+def epo_build_viewgraph(W, H, K, T, depth_dev, stride: int, tau: float, min_frac: float, stream: int = 0):
+    """Returns (frac (n, n), pairs (m, 2) int32)."""
+    import numpy as np
+    n = len(W)
+    Wa = np.ascontiguousarray(W, dtype=np.int32)
+    Ha = np.ascontiguousarray(H, dtype=np.int32)
+    Ka = np.ascontiguousarray(K, dtype=np.float64).reshape(n, 4)
+    Ta = np.ascontiguousarray(T, dtype=np.float64).reshape(n, 12)
+    frac = np.zeros((n, n))
+    pairs = np.zeros((max(n * (n - 1), 1), 2), dtype=np.int32)
+    m = ctypes.c_int32(0)
+    check(load().epo_build_viewgraph(ctypes.c_int32(n), _ptr(Wa), _ptr(Ha), _ptr(Ka), _ptr(Ta), _ptr(depth_dev),
+                                     ctypes.c_int32(stride), ctypes.c_double(tau), ctypes.c_double(min_frac),
+                                     _ptr(frac), _ptr(pairs), ctypes.byref(m), ctypes.c_void_p(stream)))
+    return frac, pairs[:m.value]
 
 
 def epo_gather_probe(n_maps: int, W: int, H: int, map_dtype: int, gather: int, pattern: int, samples: int,
