@@ -99,6 +99,8 @@ def _load():
         lib.oracle_converge_update.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_int]
         lib.oracle_viewgraph.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int, ctypes.c_double, P]
+        lib.oracle_refine_step.argtypes = [P] * 7 + [ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                                     ctypes.c_double] + [P] * 9
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -233,6 +235,32 @@ class OracleScene:
         if rc:
             raise ValueError(f"oracle_loss_grad_full failed ({rc})")
         return dict(loss=float(loss[0]), grad=grad, grad_gamma=gg, grad_alpha=ga[:n_rec], grad_beta=gb[:n_rec])
+
+    def refine_step(self, state: dict, fixed: np.ndarray, step: int, depth_t: int, lr_focal: float, lr_depth: float,
+                    *, lambda0=10.0, lambda1=6.0, lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID,
+                    lr_rot=1e-3, lr_trans=1e-2, beta1=0.9, beta2=0.999, eps=1e-12) -> float:
+        """One step of the full refinement on `state` (dict of T, gamma, alpha, beta and their Adam
+        moments m, v, mg, vg, ma, va, mb, vb; created with refine_state), updated in place.
+        Returns the loss before the step."""
+        opt = _Opt(lambda0, lambda1, lambda_steps, delta, eps_z, norm_mode, lr_rot, lr_trans, beta1, beta2, eps, 0, 0)
+        fx = np.ascontiguousarray(fixed, dtype=np.uint8)
+        loss = np.zeros(1)
+        st = state
+        rc = _load().oracle_refine_step(ctypes.byref(self._s), _p(st["T"]), _p(st["gamma"]), _p(st["alpha"]),
+                                        _p(st["beta"]), _p(fx), ctypes.byref(opt), int(step), int(depth_t),
+                                        float(lr_focal), float(lr_depth), _p(st["m"]), _p(st["v"]), _p(st["mg"]),
+                                        _p(st["vg"]), _p(st["ma"]), _p(st["va"]), _p(st["mb"]), _p(st["vb"]),
+                                        _p(loss))
+        if rc:
+            raise ValueError(f"oracle_refine_step failed ({rc})")
+        return float(loss[0])
+
+    def refine_state(self, T, gamma, alpha, beta) -> dict:
+        n, r = self.n_views, self.rec.shape[0]
+        c = lambda x, k: np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(k), dtype=np.float64).copy()
+        return dict(T=c(T, n * 12).reshape(n, 12), gamma=c(gamma, n), alpha=c(alpha, r), beta=c(beta, r),
+                    m=np.zeros((n, 6)), v=np.zeros((n, 6)), mg=np.zeros(n), vg=np.zeros(n), ma=np.zeros(r),
+                    va=np.zeros(r), mb=np.zeros(r), vb=np.zeros(r))
 
     def optimize(self, T: np.ndarray, fixed: np.ndarray, n_steps: int, *, lambda0=10.0, lambda1=6.0,
                  lambda_steps=1000, delta=1.0, eps_z=1e-6, norm_mode=NORM_VALID, lr_rot=1e-3,

@@ -865,6 +865,82 @@ double oracle_lambda(const oracle_opt* o, int64_t s) {
  * updated in place; m, v (n x 6) are the Adam moments (in/out); loss_hist
  * (n_steps, may be NULL) receives the loss evaluated before each update.
  */
+/*
+ * One step of the full refinement (Algorithm 2 with the camera and depth modules): the
+ * objective at (T, gamma, alpha, beta) with lambda of step s and its gradient, then
+ *   poses: tangent-space Adam and T <- Exp(-Delta) T as in oracle_optimize (fixed views kept);
+ *   gamma: Adam, gamma <- gamma - lr_focal m^/(sqrt(v^) + eps), bias-corrected with s + 1;
+ *   alpha, beta: the same with lr_depth and the depth step count depth_t (>= 1) when
+ *   depth_t > 0 (the depth module steps only in the schedule's second phase).
+ * m/v arrays: pose n x 6, gamma n, alpha and beta n_rec each, updated in place.
+ */
+int oracle_refine_step(const oracle_scene* S, double* T, double* gamma, double* alpha, double* beta,
+                       const uint8_t* fixed, const oracle_opt* o, int64_t s, int64_t depth_t, double lr_focal,
+                       double lr_depth, double* m, double* v, double* mg, double* vg, double* ma, double* va,
+                       double* mb, double* vb, double* loss) {
+  int n = S->n_views;
+  int64_t n_rec = S->rec_off[n];
+  double* G = (double*)malloc(sizeof(double) * 6 * n);
+  double* Gg = (double*)malloc(sizeof(double) * n);
+  double* Ga = (double*)malloc(sizeof(double) * (n_rec > 0 ? n_rec : 1));
+  double* Gb = (double*)malloc(sizeof(double) * (n_rec > 0 ? n_rec : 1));
+  if (!G || !Gg || !Ga || !Gb) {
+    free(G); free(Gg); free(Ga); free(Gb);
+    return ORACLE_ENOMEM;
+  }
+  oracle_params prm;
+  prm.lambda = oracle_lambda(o, s);
+  prm.delta = o->delta;
+  prm.eps_z = o->eps_z;
+  prm.norm_mode = o->norm_mode;
+  prm.near_margin = 0.0;
+  double L;
+  int rc = oracle_loss_grad_full(S, T, gamma, alpha, beta, &prm, &L, G, Gg, Ga, Gb);
+  if (rc) {
+    free(G); free(Gg); free(Ga); free(Gb);
+    return rc;
+  }
+  if (loss) *loss = L;
+  double bc1 = 1.0 - pow(o->beta1, (double)(s + 1)), bc2 = 1.0 - pow(o->beta2, (double)(s + 1));
+  for (int i = 0; i < n; ++i) {
+    /* focal scale of every view */
+    mg[i] = o->beta1 * mg[i] + (1.0 - o->beta1) * Gg[i];
+    vg[i] = o->beta2 * vg[i] + (1.0 - o->beta2) * Gg[i] * Gg[i];
+    gamma[i] -= lr_focal * (mg[i] / bc1) / (sqrt(vg[i] / bc2) + o->eps);
+    if (fixed && fixed[i]) continue;
+    double delta[6];
+    for (int k = 0; k < 6; ++k) {
+      double g = G[6 * i + k];
+      m[6 * i + k] = o->beta1 * m[6 * i + k] + (1.0 - o->beta1) * g;
+      v[6 * i + k] = o->beta2 * v[6 * i + k] + (1.0 - o->beta2) * g * g;
+      double lr = k < 3 ? o->lr_trans : o->lr_rot;
+      delta[k] = -lr * (m[6 * i + k] / bc1) / (sqrt(v[6 * i + k] / bc2) + o->eps);
+    }
+    double E[12], Tn[12];
+    oracle_se3_exp(delta, E);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 4; ++c) {
+        double acc = c == 3 ? E[4 * r + 3] : 0.0;
+        for (int k = 0; k < 3; ++k) acc += E[4 * r + k] * T[12 * i + 4 * k + c];
+        Tn[4 * r + c] = acc;
+      }
+    memcpy(T + 12 * i, Tn, sizeof(Tn));
+  }
+  if (depth_t > 0) {
+    double dc1 = 1.0 - pow(o->beta1, (double)depth_t), dc2 = 1.0 - pow(o->beta2, (double)depth_t);
+    for (int64_t r = 0; r < n_rec; ++r) {
+      ma[r] = o->beta1 * ma[r] + (1.0 - o->beta1) * Ga[r];
+      va[r] = o->beta2 * va[r] + (1.0 - o->beta2) * Ga[r] * Ga[r];
+      mb[r] = o->beta1 * mb[r] + (1.0 - o->beta1) * Gb[r];
+      vb[r] = o->beta2 * vb[r] + (1.0 - o->beta2) * Gb[r] * Gb[r];
+      alpha[r] -= lr_depth * (ma[r] / dc1) / (sqrt(va[r] / dc2) + o->eps);
+      beta[r] -= lr_depth * (mb[r] / dc1) / (sqrt(vb[r] / dc2) + o->eps);
+    }
+  }
+  free(G); free(Gg); free(Ga); free(Gb);
+  return ORACLE_OK;
+}
+
 int oracle_optimize(const oracle_scene* S, double* T, const uint8_t* fixed, const oracle_opt* o,
                     int64_t step0, int n_steps, double* m, double* v, double* loss_hist) {
   int n = S->n_views;
