@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define EPO_ABI_VERSION 2
+#define EPO_ABI_VERSION 3
 
 typedef enum {
   EPO_OK = 0,
@@ -129,6 +129,14 @@ typedef struct {
                                 theta_95 < sched_eps1, phase 2 (the run) after sched_w2 steps
                                 below sched_eps2, and a converged scene's poses stop changing */
   int32_t sched_w1, sched_w2; /* window sizes (defaults: the paper's 25 / 50 and 0.5 / 0.1) */
+  double lr_focal;           /* refine scenes: Adam step size of gamma (Eq. 4), applied by every
+                                epo_step with the pose update; 0 (default) keeps gamma */
+  double lr_depth;           /* refine scenes: Adam step size of alpha and beta (Eq. 5); > 0 makes
+                                each step a forward pass (the pairs' valid counts) and an adjoint
+                                pass (dL/dz per edge pixel) instead of one fused pass.  The depth
+                                module steps only in phase 2 of the schedule (Algorithm 2) when
+                                options.schedule is on, else from the first step; its Adam bias
+                                correction counts its own steps.  0 (default) keeps alpha, beta */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -256,9 +264,15 @@ epo_status epo_stage_times(epo_scene_t scene, float* ms);
  * f^0 (1 + gamma_v); alpha, beta: one float each per kept record (the records
  * of epo_scene_info.n_records, in input order without the dropped ones), the
  * record's depth is z^0 alpha + beta.  Host arrays, copied; NULL = the
- * identity (0, 1, 0).  Synchronises.  EPO_ERR_INVALID_ARG on a scene without
- * refinement or non-finite values. */
+ * identity (0, 1, 0).  Also clears the Adam moments of gamma, alpha and beta
+ * (options.lr_focal, lr_depth).  Synchronises.  EPO_ERR_INVALID_ARG on a scene
+ * without refinement or non-finite values. */
 epo_status epo_set_refinement(epo_scene_t scene, const double* gamma, const float* alpha, const float* beta);
+
+/* The current refinement (after the steps that updated it): gamma (n_views
+ * doubles), alpha and beta (n_records floats each).  Host outputs, any may be
+ * NULL.  Synchronises.  EPO_ERR_INVALID_ARG on a scene without refinement. */
+epo_status epo_get_refinement(epo_scene_t scene, double* gamma, float* alpha, float* beta);
 
 /* The objective at the current poses and refinement and its gradient with
  * respect to all of them: loss (n_scenes), grad (n_views x 6, left

@@ -39,7 +39,7 @@ EXPORTED = [
     "epo_step_async", "epo_step_plain", "epo_check", "epo_set_pair_subset", "epo_autotune",
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
-    "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph",
+    "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph", "epo_get_refinement",
 ]
 
 
@@ -74,7 +74,7 @@ class epo_options(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("pair_budget", ctypes.c_int32),
                 ("subsample_seed", ctypes.c_uint64), ("sched_eps1", ctypes.c_double),
                 ("sched_eps2", ctypes.c_double), ("schedule", ctypes.c_int32), ("sched_w1", ctypes.c_int32),
-                ("sched_w2", ctypes.c_int32)]
+                ("sched_w2", ctypes.c_int32), ("lr_focal", ctypes.c_double), ("lr_depth", ctypes.c_double)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -303,6 +303,16 @@ def epo_set_refinement(scene, gamma=None, alpha=None, beta=None):
     a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float32)
     b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
     _call("epo_set_refinement", scene, _ptr(g), _ptr(a), _ptr(b))
+
+
+def epo_get_refinement(scene, n_views: int, n_records: int):
+    """Returns (gamma (n_views,) float64, alpha, beta (n_records,) float32)."""
+    import numpy as np
+    g = np.zeros(n_views)
+    a = np.zeros(max(n_records, 1), np.float32)
+    b = np.zeros(max(n_records, 1), np.float32)
+    _call("epo_get_refinement", scene, _ptr(g), _ptr(a), _ptr(b))
+    return g, a[:n_records], b[:n_records]
 
 
 def epo_refine_loss_and_grad(scene, n_scenes: int, n_views: int, n_records: int):

@@ -123,6 +123,11 @@ struct epo_scene {
   int refine = 0;
   double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
   float *d_alpha = nullptr, *d_beta = nullptr, *d_grad_z = nullptr, *d_grad_alpha = nullptr, *d_grad_beta = nullptr;
+  // refinement optimiser: Adam moments of gamma (f64) and of alpha, beta (f32)
+  double *d_mg = nullptr, *d_vg = nullptr;
+  float *d_ma = nullptr, *d_va = nullptr, *d_mb = nullptr, *d_vb = nullptr;
+  int depth_opt = 0;           // refine && lr_depth > 0: two-pass steps and the depth update
+  int32_t max_view_records = 0;
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
@@ -281,6 +286,20 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.beta1 = S->opt.beta1;
   a.beta2 = S->opt.beta2;
   a.adam_eps = S->opt.adam_eps;
+  a.lr_focal = S->opt.lr_focal;
+  a.lr_depth = S->opt.lr_depth;
+  a.mg = S->d_mg;
+  a.vg = S->d_vg;
+  a.alpha = S->d_alpha;
+  a.beta = S->d_beta;
+  a.ma = S->d_ma;
+  a.va = S->d_va;
+  a.mb = S->d_mb;
+  a.vb = S->d_vb;
+  a.grad_z = S->d_grad_z;
+  a.rec = S->d_rec;
+  a.rec_dtype = S->rec_dtype;
+  a.max_view_records = S->max_view_records;
   return a;
 }
 
@@ -460,16 +479,32 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
 
 // One optimisation step (a1 .. a9): pair setup, edge kernel, pose kernel; no host
 // synchronisation.
+// With the depth module (refine, lr_depth > 0) the step takes two passes over the pairs, as
+// epo_refine_loss_and_grad does: the forward pass counts every pair's valid samples, which
+// weight the per-record depth derivatives of the adjoint pass; the pose kernel then updates
+// the poses and gamma, and the depth update alpha and beta.
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   StepArgs a = step_args(S, S->d_T, nullptr);
   MARK(0, s);
   if (S->subsample) CK(launch_subsample(a, s));
   if (S->refine) CK(launch_refine_intrinsics(a, s));
-  CK(launch_pair_setup(a, MODE_FUSED, s));
-  MARK(1, s);
-  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
+  epo_status st;
+  if (S->depth_opt) {
+    CK(launch_pair_setup(a, MODE_FWD, s));
+    MARK(1, s);
+    st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, s);
+    if (st != EPO_OK) return st;
+    CK(cudaMemsetAsync(S->d_grad_z, 0, (size_t)std::max<int64_t>(S->n_records, 1) * 4, s));
+    CK(launch_pair_setup(a, MODE_BWD, s));
+    st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, s);
+  } else {
+    CK(launch_pair_setup(a, MODE_FUSED, s));
+    MARK(1, s);
+    st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
+  }
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 2, s));
+  if (S->depth_opt) CK(launch_depth_update(a, s));
   if (S->opt.schedule) CK(launch_schedule(a, s));
   MARK(3, s);
   return EPO_OK;
@@ -530,7 +565,12 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "schedule windows must be >= 1 and thresholds >= 0");
   if (o.refine && o.records_per_thread != 0 && o.records_per_thread != 2)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "refine scenes run two records per thread");
+  if (!(o.lr_focal >= 0) || !(o.lr_depth >= 0) || !isfinite(o.lr_focal) || !isfinite(o.lr_depth))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "lr_focal and lr_depth must be finite and >= 0");
+  if (!o.refine && (o.lr_focal != 0 || o.lr_depth != 0))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "lr_focal and lr_depth need options.refine = 1");
   S->refine = o.refine;
+  S->depth_opt = o.refine && o.lr_depth > 0;
   S->stream = (cudaStream_t)cuda_stream;
   const int rec_dtype = descs[0].record_dtype, map_dtype = descs[0].map_dtype;
   if (rec_dtype != EPO_F32 && rec_dtype != EPO_F16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown record dtype");
@@ -777,6 +817,13 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       ALLOC(S->d_grad_z, nr);
       ALLOC(S->d_grad_alpha, nr);
       ALLOC(S->d_grad_beta, nr);
+      ALLOC(S->d_mg, nv);
+      ALLOC(S->d_vg, nv);
+      ALLOC(S->d_ma, nr);
+      ALLOC(S->d_va, nr);
+      ALLOC(S->d_mb, nr);
+      ALLOC(S->d_vb, nr);
+      for (const ViewDev& w : S->views) S->max_view_records = std::max(S->max_view_records, w.n_rec);
     }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
     cudaStream_t st = S->stream;
@@ -1029,7 +1076,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule;
+  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule + 3 * S->depth_opt;
   info->tail_pairs = S->tail;
   return EPO_OK;
 }
@@ -1245,10 +1292,24 @@ epo_status epo_set_refinement(epo_scene_t S, const double* gamma, const float* a
   for (size_t r = 0; r < nr; ++r)
     if (!isfinite(al[r]) || !isfinite(be[r])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite alpha or beta");
   CK(cudaMemcpyAsync(S->d_gamma, g.data(), nv * 8, cudaMemcpyHostToDevice, S->stream));
+  CK(cudaMemsetAsync(S->d_mg, 0, nv * 8, S->stream));
+  CK(cudaMemsetAsync(S->d_vg, 0, nv * 8, S->stream));
   if (nr) {
     CK(cudaMemcpyAsync(S->d_alpha, al.data(), nr * 4, cudaMemcpyHostToDevice, S->stream));
     CK(cudaMemcpyAsync(S->d_beta, be.data(), nr * 4, cudaMemcpyHostToDevice, S->stream));
+    for (float* q : {S->d_ma, S->d_va, S->d_mb, S->d_vb}) CK(cudaMemsetAsync(q, 0, nr * 4, S->stream));
   }
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_refinement(epo_scene_t S, double* gamma, float* alpha, float* beta) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
+  const size_t nv = (size_t)S->n_views, nr = (size_t)S->n_records;
+  if (gamma) CK(cudaMemcpyAsync(gamma, S->d_gamma, nv * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (alpha && nr) CK(cudaMemcpyAsync(alpha, S->d_alpha, nr * 4, cudaMemcpyDeviceToHost, S->stream));
+  if (beta && nr) CK(cudaMemcpyAsync(beta, S->d_beta, nr * 4, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   return EPO_OK;
 }

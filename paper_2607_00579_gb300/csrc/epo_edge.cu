@@ -526,6 +526,58 @@ cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad
   return cudaGetLastError();
 }
 
+// Depth module of the refinement optimiser (Algorithm 2; Eq. 5): Adam on alpha_r and beta_r of
+// every record from dL/dz_r of the adjoint pass, after the pose kernel (which advanced the step
+// counter unless the step was refused).  With the schedule a scene's depth module steps only in
+// phase 2, counting its own steps from the switch (phase-2 steps s > s_switch are its steps
+// 1, 2, ...); without it, from the first step.  Blocks are (view, chunk of the view's records).
+constexpr int kDepthThreads = 256;
+constexpr int kDepthPerThread = 4;
+
+template <int REC>
+__global__ void __launch_bounds__(kDepthThreads) k_depth_update(StepArgs a, int chunks_per_view) {
+  if (*a.flag & 1) return;  // refused step: nothing moves
+  const int v = blockIdx.x / chunks_per_view, ch = blockIdx.x % chunks_per_view;
+  const ViewDev vd = a.views[v];
+  const int sc = vd.scene;
+  const int64_t s_cur = *a.step - 1;  // the step just taken
+  int64_t dt;
+  if (a.schedule) {
+    if (a.sched_state[2 * sc] != 2) return;  // phase 1, or converged
+    dt = s_cur - a.sched_steps[2 * sc];
+  } else {
+    dt = s_cur + 1;
+  }
+  if (dt < 1) return;
+  const float c1 = (float)(1.0 - pow(a.beta1, (double)dt)), c2 = (float)(1.0 - pow(a.beta2, (double)dt));
+  const float b1 = (float)a.beta1, b2 = (float)a.beta2, lr = (float)a.lr_depth, eps = (float)a.adam_eps;
+  const int64_t r0 = vd.rec_begin, n = vd.n_rec;
+  for (int64_t k = (int64_t)ch * kDepthThreads + threadIdx.x; k < n; k += (int64_t)chunks_per_view * kDepthThreads) {
+    const int64_t r = r0 + k;
+    float u, w, z0;
+    load_record<REC>(a.rec, r, u, w, z0);
+    const float gb = a.grad_z[r], ga = gb * z0;
+    const float ma = b1 * a.ma[r] + (1.f - b1) * ga, va = b2 * a.va[r] + (1.f - b2) * ga * ga;
+    const float mb = b1 * a.mb[r] + (1.f - b1) * gb, vb = b2 * a.vb[r] + (1.f - b2) * gb * gb;
+    a.ma[r] = ma;
+    a.va[r] = va;
+    a.mb[r] = mb;
+    a.vb[r] = vb;
+    a.alpha[r] -= lr * (ma / c1) / (sqrtf(va / c2) + eps);
+    a.beta[r] -= lr * (mb / c1) / (sqrtf(vb / c2) + eps);
+  }
+}
+
+cudaError_t launch_depth_update(const StepArgs& a, cudaStream_t s) {
+  if (a.max_view_records <= 0 || a.n_views <= 0) return cudaSuccess;
+  const int cpv = (int)std::max<int64_t>(
+      1, ((int64_t)a.max_view_records + kDepthThreads * kDepthPerThread - 1) / (kDepthThreads * kDepthPerThread));
+  const unsigned nb = (unsigned)((int64_t)cpv * a.n_views);
+  if (a.rec_dtype) k_depth_update<1><<<nb, kDepthThreads, 0, s>>>(a, cpv);
+  else k_depth_update<0><<<nb, kDepthThreads, 0, s>>>(a, cpv);
+  return cudaGetLastError();
+}
+
 size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine) {
   // dynamic part: lifted records, raw (u, v), per-warp per-pair partial sums
   return sizeof(float4) * (size_t)rpt * block + sizeof(float2) * (size_t)rpt * block +

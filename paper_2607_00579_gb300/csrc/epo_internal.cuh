@@ -119,7 +119,7 @@ struct StepArgs {
   // focal refinement (refine scenes): gamma per view, the FP64 base intrinsics and their
   // refined copy written by the pair setup, the per-pair focal sums and the focal gradient
   int32_t refine;
-  const double* gamma;
+  double* gamma;                     // updated by the pose kernel's focal Adam (lr_focal)
   const double* K64;                 // n_views x 6: fx, fy, cx, cy, 1/fx, 1/fy (base)
   double* K64r;                      // the same at f0 (1 + gamma)
   double* pair_facc;                 // n_pairs x 2
@@ -181,6 +181,20 @@ struct StepArgs {
   double inv_lambda_steps;
   int32_t norm_all;
   double lr_rot, lr_trans, beta1, beta2, adam_eps;
+  // refinement optimiser (Algorithm 2 with the camera and depth modules)
+  double lr_focal, lr_depth;
+  double* mg;                        // n_views Adam moments of gamma (f64)
+  double* vg;
+  float* alpha;                      // n_records: z = z0 alpha + beta
+  float* beta;
+  float* ma;                         // n_records Adam moments of alpha and beta (f32)
+  float* va;
+  float* mb;
+  float* vb;
+  const float* grad_z;               // n_records: dL/dz of the adjoint pass
+  const void* rec;                   // records (z0)
+  int32_t rec_dtype;
+  int32_t max_view_records;          // most records of one view (grid of the depth update)
 };
 
 // ---- launchers (epo_kernels.cu) ----
@@ -188,6 +202,7 @@ cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_schedule(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_depth_update(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
                                float* grad_beta, int64_t n, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);

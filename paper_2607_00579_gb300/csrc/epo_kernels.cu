@@ -171,6 +171,11 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       bp0 = a.bpow[0];
       bp1 = a.bpow[1];
     }
+    double mg_old = 0.0, vg_old = 0.0;
+    if (with_grad == 2 && vv && a.refine && e == 0) {
+      mg_old = a.mg[v];
+      vg_old = a.vg[v];
+    }
     // a scene whose schedule has converged keeps its poses
     const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
     double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -217,7 +222,24 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       for (int k = 0; k < 6; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
       if (a.refine) gg += __shfl_xor_sync(0xffffffffu, gg, o);
     }
-    if (a.refine && vv && e == 0 && a.grad_gamma) a.grad_gamma[v] = gg / (1.0 + a.gamma[v]);
+    if (a.refine && vv && e == 0) {
+      const double g0 = a.gamma[v];
+      const double Gg = gg / (1.0 + g0);  // dL/dgamma_v
+      if (a.grad_gamma) a.grad_gamma[v] = Gg;
+      if (with_grad == 2) {
+        // Adam on the focal scale (Eq. 4), every step, in FP64 (one lane per view); the bias
+        // factors are the pose optimiser's (the same step count)
+        if (!isfinite(Gg)) {
+          atomicOr(a.flag, 1);
+        } else if (!(flag0 & 1) && !conv) {
+          const double m = a.beta1 * mg_old + (1.0 - a.beta1) * Gg;
+          const double vm = a.beta2 * vg_old + (1.0 - a.beta2) * Gg * Gg;
+          a.mg[v] = m;
+          a.vg[v] = vm;
+          a.gamma[v] = g0 - a.lr_focal * (m / (1.0 - bp0)) / (sqrt(vm / (1.0 - bp1)) + a.adam_eps);
+        }
+      }
+    }
     double G = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; ++k)
@@ -237,9 +259,10 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         const double vm = a.beta2 * v_old + (1.0 - a.beta2) * G * G;
         a.m[o] = m;
         a.v[o] = vm;
-        // the step ratio m^ / (sqrt(v^) + eps) needs only single precision
-        const float mh = (float)m / (1.f - (float)bp0);
-        const float vh = (float)vm / (1.f - (float)bp1);
+        // the step ratio m^ / (sqrt(v^) + eps) needs only single precision; the bias factors
+        // 1 - beta^(s+1) are formed in FP64 (in FP32, 1 - beta2 cancels to ~1e-5 relative)
+        const float mh = (float)m / (float)(1.0 - bp0);
+        const float vh = (float)vm / (float)(1.0 - bp1);
         const float lr = (float)(e < 3 ? a.lr_trans : a.lr_rot);
         xi = -(double)(lr * mh / (sqrtf(vh) + (float)a.adam_eps));  // the update is Exp(-Delta)
       }
