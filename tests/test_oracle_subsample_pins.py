@@ -3,12 +3,15 @@ uniform random subset of min(|E|, M) pairs every step).  The random keys come fr
 (Steele, Lea and Flood, OOPSLA 2014), whose reference sequence from seed 0 is published; the
 subset must have the stated size, and over many steps every pair, and every couple of pairs,
 must be drawn with the frequencies of a uniform subset."""
+from pathlib import Path
+
 import numpy as np
 
 import oracle
 
-# SplitMix64's first outputs from seed 0 (the generator's reference sequence)
-SPLITMIX64_SEED0 = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+# SplitMix64's first outputs from seed 0 (the generator's published reference sequence)
+_GOLDEN = (Path(__file__).parent / "golden" / "splitmix64_seed0.txt").read_text().splitlines()
+SPLITMIX64_SEED0 = [int(ln.split()[0], 16) for ln in _GOLDEN if ln.strip() and not ln.startswith("#")]
 
 
 def test_splitmix64_reference_sequence():
