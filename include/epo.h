@@ -131,9 +131,9 @@ typedef struct {
   int32_t sched_w1, sched_w2; /* window sizes (defaults: the paper's 25 / 50 and 0.5 / 0.1) */
   double lr_focal;           /* refine scenes: Adam step size of gamma (Eq. 4), applied by every
                                 epo_step with the pose update; 0 (default) keeps gamma */
-  double lr_depth;           /* refine scenes: Adam step size of alpha and beta (Eq. 5); > 0 makes
-                                each step a forward pass (the pairs' valid counts) and an adjoint
-                                pass (dL/dz per edge pixel) instead of one fused pass.  The depth
+  double lr_depth;           /* refine scenes: Adam step size of alpha and beta (Eq. 5); > 0 adds
+                                the depth kernel to every step (dL/dz per edge pixel from the
+                                fused pass's per-sample derivatives, then Adam).  The depth
                                 module steps only in phase 2 of the schedule (Algorithm 2) when
                                 options.schedule is on, else from the first step; its Adam bias
                                 correction counts its own steps.  0 (default) keeps alpha, beta */
@@ -277,10 +277,10 @@ epo_status epo_get_refinement(epo_scene_t scene, double* gamma, float* alpha, fl
 /* The objective at the current poses and refinement and its gradient with
  * respect to all of them: loss (n_scenes), grad (n_views x 6, left
  * perturbation), grad_gamma (n_views), grad_alpha and grad_beta (n_records,
- * dL/dalpha = dL/dz z^0, dL/dbeta = dL/dz).  Two passes (Algorithm 2's
- * forward and analytic backward): the forward counts every pair's valid
- * samples, which weight the per-record depth derivatives of the adjoint.
- * Host outputs; any gradient may be NULL.  Synchronises. */
+ * dL/dalpha = dL/dz z^0, dL/dbeta = dL/dz).  One fused pass stores every
+ * sample's d(rho)/dz (4 bytes per evaluation of library memory); a second
+ * kernel weights them by the pairs' w / n once the pass has counted the valid
+ * samples.  Host outputs; any gradient may be NULL.  Synchronises. */
 epo_status epo_refine_loss_and_grad(epo_scene_t scene, double* loss, double* grad, double* grad_gamma,
                                     float* grad_alpha, float* grad_beta);
 

@@ -122,11 +122,13 @@ struct epo_scene {
   // focal and depth refinement (options.refine)
   int refine = 0;
   double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
-  float *d_alpha = nullptr, *d_beta = nullptr, *d_grad_z = nullptr, *d_grad_alpha = nullptr, *d_grad_beta = nullptr;
+  float *d_alpha = nullptr, *d_beta = nullptr, *d_grad_alpha = nullptr, *d_grad_beta = nullptr;
+  float* d_dzr = nullptr;  // per (pair, source record) d(rho)/dz of the fused pass
+  int64_t n_dzr = 0;       // sum over pairs of the source view's records
   // refinement optimiser: Adam moments of gamma (f64) and of alpha, beta (f32)
   double *d_mg = nullptr, *d_vg = nullptr;
   float *d_ma = nullptr, *d_va = nullptr, *d_mb = nullptr, *d_vb = nullptr;
-  int depth_opt = 0;           // refine && lr_depth > 0: two-pass steps and the depth update
+  int depth_opt = 0;           // refine && lr_depth > 0: the depth module's kernel in every step
   int32_t max_view_records = 0;
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
@@ -296,7 +298,11 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.va = S->d_va;
   a.mb = S->d_mb;
   a.vb = S->d_vb;
-  a.grad_z = S->d_grad_z;
+  a.dzr = S->d_dzr;
+  a.src_pair_off = S->d_src_pair_off;
+  a.src_pair_ids = S->d_src_pair_ids;
+  a.grad_alpha = S->d_grad_alpha;
+  a.grad_beta = S->d_grad_beta;
   a.rec = S->d_rec;
   a.rec_dtype = S->rec_dtype;
   a.max_view_records = S->max_view_records;
@@ -402,7 +408,7 @@ EdgeArgs edge_args(epo_scene* S) {
     a.alpha = S->d_alpha;
     a.beta = S->d_beta;
     a.pair_facc = S->d_pair_facc;
-    a.grad_z = S->d_grad_z;
+    a.dzr = S->d_dzr;
   }
   a.pair_lw = S->d_pair_lw;
   a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
@@ -479,32 +485,20 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
 
 // One optimisation step (a1 .. a9): pair setup, edge kernel, pose kernel; no host
 // synchronisation.
-// With the depth module (refine, lr_depth > 0) the step takes two passes over the pairs, as
-// epo_refine_loss_and_grad does: the forward pass counts every pair's valid samples, which
-// weight the per-record depth derivatives of the adjoint pass; the pose kernel then updates
-// the poses and gamma, and the depth update alpha and beta.
+// Refine scenes: the fused pass also stores every sample's d(rho)/dz; the pose kernel updates
+// the poses and gamma, and with the depth module (lr_depth > 0) the depth kernel weights those
+// derivatives by the pairs' w / n and updates alpha and beta.
 epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   StepArgs a = step_args(S, S->d_T, nullptr);
   MARK(0, s);
   if (S->subsample) CK(launch_subsample(a, s));
   if (S->refine) CK(launch_refine_intrinsics(a, s));
-  epo_status st;
-  if (S->depth_opt) {
-    CK(launch_pair_setup(a, MODE_FWD, s));
-    MARK(1, s);
-    st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, s);
-    if (st != EPO_OK) return st;
-    CK(cudaMemsetAsync(S->d_grad_z, 0, (size_t)std::max<int64_t>(S->n_records, 1) * 4, s));
-    CK(launch_pair_setup(a, MODE_BWD, s));
-    st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, s);
-  } else {
-    CK(launch_pair_setup(a, MODE_FUSED, s));
-    MARK(1, s);
-    st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
-  }
+  CK(launch_pair_setup(a, MODE_FUSED, s));
+  MARK(1, s);
+  epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 2, s));
-  if (S->depth_opt) CK(launch_depth_update(a, s));
+  if (S->depth_opt) CK(launch_depth(a, 1, s));
   if (S->opt.schedule) CK(launch_schedule(a, s));
   MARK(3, s);
   return EPO_OK;
@@ -713,6 +707,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   }
   S->evals = 0;
   for (int p = 0; p < np; ++p) S->evals += S->views[S->pair_src[p]].n_rec;
+  S->n_dzr = S->refine ? S->evals : 0;  // one d(rho)/dz per evaluation of a refine scene
   for (int sc = 0; sc < n_scenes; ++sc)
     if (o.pair_budget > 0 && S->scene_pair_off[sc + 1] - S->scene_pair_off[sc] > o.pair_budget) S->subsample = 1;
   // ---- device allocations (CK / ALLOC report into the handle under construction) ----
@@ -814,7 +809,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       const size_t nr = (size_t)std::max<int64_t>(S->n_records, 1);
       ALLOC(S->d_alpha, nr);
       ALLOC(S->d_beta, nr);
-      ALLOC(S->d_grad_z, nr);
+      ALLOC(S->d_dzr, (size_t)std::max<int64_t>(S->n_dzr, 1));
       ALLOC(S->d_grad_alpha, nr);
       ALLOC(S->d_grad_beta, nr);
       ALLOC(S->d_mg, nv);
@@ -951,6 +946,14 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
         q.map_off = vj.map_off;
         q.tex = th[S->pair_dst[p]];
       }
+      if (S->refine) {  // each pair's block of d(rho)/dz values, one per source record
+        int64_t run = 0;
+        for (int v = 0; v < nv; ++v)
+          for (int k = S->src_pair_off[v]; k < S->src_pair_off[v + 1]; ++k) {
+            pp[S->src_pair_ids[k]].dbase = run - S->views[v].rec_begin;
+            run += S->views[v].n_rec;
+          }
+      }
       CK(cudaMemcpyAsync(S->d_pp, pp.data(), (size_t)np * sizeof(PairParam), cudaMemcpyHostToDevice, st));
       CK(cudaStreamSynchronize(st));
     }
@@ -1076,7 +1079,7 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule + 3 * S->depth_opt;
+  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule + S->depth_opt;
   info->tail_pairs = S->tail;
   return EPO_OK;
 }
@@ -1322,20 +1325,15 @@ epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, d
   if (st != EPO_OK) return st;
   cudaStream_t s = S->stream;
   StepArgs a = step_args(S, S->d_T, nullptr);
-  // forward: the loss and every pair's valid count (the pair means' denominators)
+  // one fused pass: the loss, the pose and focal sums per pair, every sample's d(rho)/dz; then
+  // the per-record depth gradients weighted by the pairs' w / n
   if (S->subsample) CK(launch_subsample(a, s));
   CK(launch_refine_intrinsics(a, s));
-  CK(launch_pair_setup(a, MODE_FWD, s));
-  st = run_edge(S, MODE_FWD, S->gather, S->rpt, S->block, S->tail, s);
-  if (st != EPO_OK) return st;
-  CK(launch_poses(a, 0, s));
-  // adjoint: pose and focal sums per pair, dL/dz per record with the pairs' weights
-  CK(cudaMemsetAsync(S->d_grad_z, 0, (size_t)std::max<int64_t>(S->n_records, 1) * 4, s));
-  CK(launch_pair_setup(a, MODE_BWD, s));
-  st = run_edge(S, MODE_BWD, S->gather, S->rpt, S->block, S->tail, s);
+  CK(launch_pair_setup(a, MODE_FUSED, s));
+  st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 1, s));
-  CK(launch_depth_grads(S->d_rec, S->rec_dtype, S->d_grad_z, S->d_grad_alpha, S->d_grad_beta, S->n_records, s));
+  CK(launch_depth(a, 0, s));
   CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, s));
   if (grad) CK(cudaMemcpyAsync(grad, S->d_grad, (size_t)S->n_views * 48, cudaMemcpyDeviceToHost, s));
   if (grad_gamma) CK(cudaMemcpyAsync(grad_gamma, S->d_grad_gamma, (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, s));

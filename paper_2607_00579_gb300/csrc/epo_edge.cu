@@ -28,20 +28,6 @@ namespace epo {
 // ------------------------------------------------------------------------------------
 // a2-a7: the edge kernel
 // ------------------------------------------------------------------------------------
-template <int REC>
-__device__ __forceinline__ void load_record(const void* base, int64_t idx, float& u, float& v,
-                                            float& z) {
-  if (REC == 0) {  // EPO_F32: {u, v, z, 0}
-    float4 r = __ldg(reinterpret_cast<const float4*>(base) + idx);
-    u = r.x; v = r.y; z = r.z;
-  } else {         // EPO_F16: {u16 u, u16 v, f16 z, u16 0}
-    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
-    u = (float)(r.x & 0xffffu);
-    v = (float)(r.x >> 16);
-    z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
-  }
-}
-
 
 // 2x2 footprint (x0, y0) .. (x0+1, y0+1) of a map.
 template <int MAP, int GATHER>
@@ -214,11 +200,7 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, d
         const float gr2 = gx * r[2] + gy * r[5] + gz * r[8];
         atomicAdd(a.pair_facc + 2 * (size_t)p, (double)(zf * (gr2 - dz)));
         atomicAdd(a.pair_facc + 2 * (size_t)p + 1, (double)(gx * y0f + gy * y1f));
-        if constexpr (MODE == MODE_BWD) {
-          const double n = acc[1];
-          const float w = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
-          atomicAdd(a.grad_z + rec, w * dz);
-        }
+        if constexpr (MODE == MODE_FUSED) a.dzr[P.dbase + rec] = dz;  // the fast path wrote 0
       }
     }
   }
@@ -297,9 +279,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     // registers across the pair loop costs a block per SM)
     const int pb = __ldg(&a.tiles[t].q0);
     const int pe = __ldg(&a.tiles[t].q1);
-    float gzr[REF && MODE == MODE_BWD ? RPT : 1];  // refine adjoint: dL/dz of the thread's records
-#pragma unroll
-    for (int r = 0; r < (REF && MODE == MODE_BWD ? RPT : 1); ++r) gzr[r] = 0.f;
     for (int q = pb; q < pe; ++q) {
       const int p = a.src_pair_ids[q];
       if (!a.pair_active[p]) continue;  // uniform over the block
@@ -309,11 +288,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc[k] = 0.f;
       float facc0 = 0.f, facc1 = 0.f;  // refine: source- and target-focal sums
-      float wp = 0.f;                  // refine adjoint: the pair's weight in the loss
-      if constexpr (REF && MODE == MODE_BWD) {
-        const double n = a.pair_acc[(size_t)kAcc * p + 1];  // valid samples, from the forward pass
-        wp = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
-      }
       // the thread's RPT records, ILP of them in flight at a time: one reduction per pair
       // for all RPT samples, registers for only ILP
       constexpr int ILP = RPT < 2 ? RPT : 2;
@@ -413,6 +387,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
               }
             }
           }
+          float dzs = 0.f;  // refine, fused pass: the sample's d(rho)/dz (0 unless valid)
           if (ok[r]) {
             // a5: clamp + Huber
             const float dh = fminf(d, lam);
@@ -447,9 +422,16 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
                 const float gr2 = gx * P.r[2] + gy * P.r[5] + gz * P.r[8];
                 facc0 += zr * (gr2 - dz);
                 facc1 += gx * Y0[r] + gy * Y1[r];
-                if constexpr (MODE == MODE_BWD) gzr[g + r] += wp * dz;
+                dzs = dz;
               }
             }
+          }
+          if constexpr (REF && MODE == MODE_FUSED) {
+            // every record of the tile gets its value for this pair (an ambiguous sample's is
+            // written again by the exact path after the block barrier); the depth kernel
+            // weights them by the pairs' w / n once the pass has counted the valid samples
+            const int li = threadIdx.x + (g + r) * blockDim.x;
+            if (li < td.n) a.dzr[P.dbase + td.begin + li] = dzs;
           }
         }
       }
@@ -464,13 +446,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
         }
         if (lane == 8 || lane == 9)
           s_part[((size_t)warp * a.max_pairs + (q - pb)) * NSLOT + lane] = lane == 8 ? facc0 : facc1;
-      }
-    }
-    if constexpr (REF && MODE == MODE_BWD) {
-#pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int idx = threadIdx.x + r * blockDim.x;
-        if (idx < td.n && gzr[r] != 0.f) atomicAdd(a.grad_z + td.begin + idx, gzr[r]);
       }
     }
     __syncthreads();  // every warp has stored its partial sums for this tile
@@ -503,79 +478,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       __syncthreads();
     }
   }
-}
-
-// dL/dalpha_r = dL/dz_r Z0_r and dL/dbeta_r = dL/dz_r (z_r = Z0_r alpha_r + beta_r, Eq. 5).
-template <int REC>
-__global__ void k_depth_grads(const void* rec, const float* grad_z, float* grad_alpha, float* grad_beta, int64_t n) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    float u, v, z0;
-    load_record<REC>(rec, r, u, v, z0);
-    const float gz = grad_z[r];
-    if (grad_alpha) grad_alpha[r] = gz * z0;
-    if (grad_beta) grad_beta[r] = gz;
-  }
-}
-
-cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
-                               float* grad_beta, int64_t n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int nb = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  if (rec_dtype) k_depth_grads<1><<<nb, 256, 0, s>>>(rec, grad_z, grad_alpha, grad_beta, n);
-  else k_depth_grads<0><<<nb, 256, 0, s>>>(rec, grad_z, grad_alpha, grad_beta, n);
-  return cudaGetLastError();
-}
-
-// Depth module of the refinement optimiser (Algorithm 2; Eq. 5): Adam on alpha_r and beta_r of
-// every record from dL/dz_r of the adjoint pass, after the pose kernel (which advanced the step
-// counter unless the step was refused).  With the schedule a scene's depth module steps only in
-// phase 2, counting its own steps from the switch (phase-2 steps s > s_switch are its steps
-// 1, 2, ...); without it, from the first step.  Blocks are (view, chunk of the view's records).
-constexpr int kDepthThreads = 256;
-constexpr int kDepthPerThread = 4;
-
-template <int REC>
-__global__ void __launch_bounds__(kDepthThreads) k_depth_update(StepArgs a, int chunks_per_view) {
-  if (*a.flag & 1) return;  // refused step: nothing moves
-  const int v = blockIdx.x / chunks_per_view, ch = blockIdx.x % chunks_per_view;
-  const ViewDev vd = a.views[v];
-  const int sc = vd.scene;
-  const int64_t s_cur = *a.step - 1;  // the step just taken
-  int64_t dt;
-  if (a.schedule) {
-    if (a.sched_state[2 * sc] != 2) return;  // phase 1, or converged
-    dt = s_cur - a.sched_steps[2 * sc];
-  } else {
-    dt = s_cur + 1;
-  }
-  if (dt < 1) return;
-  const float c1 = (float)(1.0 - pow(a.beta1, (double)dt)), c2 = (float)(1.0 - pow(a.beta2, (double)dt));
-  const float b1 = (float)a.beta1, b2 = (float)a.beta2, lr = (float)a.lr_depth, eps = (float)a.adam_eps;
-  const int64_t r0 = vd.rec_begin, n = vd.n_rec;
-  for (int64_t k = (int64_t)ch * kDepthThreads + threadIdx.x; k < n; k += (int64_t)chunks_per_view * kDepthThreads) {
-    const int64_t r = r0 + k;
-    float u, w, z0;
-    load_record<REC>(a.rec, r, u, w, z0);
-    const float gb = a.grad_z[r], ga = gb * z0;
-    const float ma = b1 * a.ma[r] + (1.f - b1) * ga, va = b2 * a.va[r] + (1.f - b2) * ga * ga;
-    const float mb = b1 * a.mb[r] + (1.f - b1) * gb, vb = b2 * a.vb[r] + (1.f - b2) * gb * gb;
-    a.ma[r] = ma;
-    a.va[r] = va;
-    a.mb[r] = mb;
-    a.vb[r] = vb;
-    a.alpha[r] -= lr * (ma / c1) / (sqrtf(va / c2) + eps);
-    a.beta[r] -= lr * (mb / c1) / (sqrtf(vb / c2) + eps);
-  }
-}
-
-cudaError_t launch_depth_update(const StepArgs& a, cudaStream_t s) {
-  if (a.max_view_records <= 0 || a.n_views <= 0) return cudaSuccess;
-  const int cpv = (int)std::max<int64_t>(
-      1, ((int64_t)a.max_view_records + kDepthThreads * kDepthPerThread - 1) / (kDepthThreads * kDepthPerThread));
-  const unsigned nb = (unsigned)((int64_t)cpv * a.n_views);
-  if (a.rec_dtype) k_depth_update<1><<<nb, kDepthThreads, 0, s>>>(a, cpv);
-  else k_depth_update<0><<<nb, kDepthThreads, 0, s>>>(a, cpv);
-  return cudaGetLastError();
 }
 
 size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine) {

@@ -21,6 +21,7 @@
 //              on device so that a whole optimisation step is a replayable CUDA graph.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,22 @@ namespace epo {
 constexpr float kU32 = 5.9604645e-08f;
 
 __device__ __forceinline__ float bf16_bits_to_float(unsigned int b) { return __uint_as_float(b << 16); }
+
+// One edge record: EPO_F32 {f32 u, f32 v, f32 z, 0} (REC 0) or EPO_F16 {u16 u, u16 v, f16 z, 0}.
+template <int REC>
+__device__ __forceinline__ void load_record(const void* base, int64_t idx, float& u, float& v, float& z) {
+  if (REC == 0) {
+    float4 r = __ldg(reinterpret_cast<const float4*>(base) + idx);
+    u = r.x;
+    v = r.y;
+    z = r.z;
+  } else {
+    uint2 r = __ldg(reinterpret_cast<const uint2*>(base) + idx);
+    u = (float)(r.x & 0xffffu);
+    v = (float)(r.x >> 16);
+    z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+  }
+}
 
 constexpr int kAcc = 8;
 constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)  // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
@@ -70,6 +87,7 @@ struct alignas(16) PairParam {
   int32_t W, H, pitch;    // target map
   int64_t map_off;
   unsigned long long tex; // texture object of the target map
+  int64_t dbase;          // refine scenes: dzr[dbase + r] holds d(rho)/dz of record r for this pair
 };
 static_assert(sizeof(PairParam) == 128, "PairParam layout");
 
@@ -101,7 +119,8 @@ struct EdgeArgs {
   const float* alpha;            // n_records: z = z0 alpha + beta
   const float* beta;
   double* pair_facc;             // n_pairs x 2: sums of the source- and target-focal terms
-  float* grad_z;                 // n_records: dL/dz (adjoint pass only)
+  float* dzr;                    // per (pair, source record): d(rho)/dz of the sample, 0 if it is
+                                 // invalid (fused pass of refine scenes; at PairParam::dbase + r)
   const double* pair_lw;         // n_pairs: the pair's weight in its scene's loss
   int32_t norm_all;
 };
@@ -191,7 +210,11 @@ struct StepArgs {
   float* va;
   float* mb;
   float* vb;
-  const float* grad_z;               // n_records: dL/dz of the adjoint pass
+  const float* dzr;                  // per (pair, record) d(rho)/dz of the fused pass
+  const int32_t* src_pair_off;       // n_views + 1: the view's outgoing pairs in src_pair_ids
+  const int32_t* src_pair_ids;
+  float* grad_alpha;                 // n_records (gradient mode of the depth kernel)
+  float* grad_beta;
   const void* rec;                   // records (z0)
   int32_t rec_dtype;
   int32_t max_view_records;          // most records of one view (grid of the depth update)
@@ -202,9 +225,8 @@ cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_schedule(const StepArgs& a, cudaStream_t s);
-cudaError_t launch_depth_update(const StepArgs& a, cudaStream_t s);
-cudaError_t launch_depth_grads(const void* rec, int rec_dtype, const float* grad_z, float* grad_alpha,
-                               float* grad_beta, int64_t n, cudaStream_t s);
+// depth kernel: update 0 = dL/dalpha, dL/dbeta into grad_alpha, grad_beta; 1 = Adam step
+cudaError_t launch_depth(const StepArgs& a, int update, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);
 cudaError_t launch_edge(const EdgeArgs& a, int mode, int refine, int rec_dtype, int map_dtype, int gather,
                         int rpt, int block, int grid, cudaStream_t s);
