@@ -124,6 +124,7 @@ struct epo_scene {
   double *d_gamma = nullptr, *d_K64r = nullptr, *d_pair_facc = nullptr, *d_grad_gamma = nullptr;
   float *d_alpha = nullptr, *d_beta = nullptr, *d_grad_alpha = nullptr, *d_grad_beta = nullptr;
   float* d_dzr = nullptr;  // per (pair, source record) d(rho)/dz of the fused pass
+  float* d_pair_wz = nullptr;  // per pair w / n of the last evaluation (refine scenes)
   int64_t n_dzr = 0;       // sum over pairs of the source view's records
   // refinement optimiser: Adam moments of gamma (f64) and of alpha, beta (f32)
   double *d_mg = nullptr, *d_vg = nullptr;
@@ -290,6 +291,8 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.adam_eps = S->opt.adam_eps;
   a.lr_focal = S->opt.lr_focal;
   a.lr_depth = S->opt.lr_depth;
+  a.log_beta1 = (float)log(S->opt.beta1);
+  a.log_beta2 = (float)log(S->opt.beta2);
   a.mg = S->d_mg;
   a.vg = S->d_vg;
   a.alpha = S->d_alpha;
@@ -299,6 +302,7 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.mb = S->d_mb;
   a.vb = S->d_vb;
   a.dzr = S->d_dzr;
+  a.pair_wz = S->d_pair_wz;
   a.src_pair_off = S->d_src_pair_off;
   a.src_pair_ids = S->d_src_pair_ids;
   a.grad_alpha = S->d_grad_alpha;
@@ -810,6 +814,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       ALLOC(S->d_alpha, nr);
       ALLOC(S->d_beta, nr);
       ALLOC(S->d_dzr, (size_t)std::max<int64_t>(S->n_dzr, 1));
+      ALLOC(S->d_pair_wz, np);
       ALLOC(S->d_grad_alpha, nr);
       ALLOC(S->d_grad_beta, nr);
       ALLOC(S->d_mg, nv);

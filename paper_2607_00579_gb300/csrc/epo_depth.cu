@@ -22,76 +22,112 @@
 
 namespace epo {
 
-// Blocks are (view, chunk of the view's records).  The block's first threads form the weights
-// of the view's pairs in shared memory (0 for an inactive pair, whose values were not written
+// Blocks are (view, chunk of the view's records).  The block's first warp lists the view's
+// active pairs in shared memory with their weights (an inactive pair's values were not written
 // this pass).  Update mode runs after the pose kernel, which advanced the step counter unless
 // the step was refused; with the schedule a scene's depth module steps only in phase 2 and
 // counts its own steps from the switch (the phase-2 steps s > s_switch are its steps 1, 2, ...),
-// without it from the first step; the bias factors are formed once per block in FP64.
-constexpr int kDepthThreads = 256;
-constexpr int kDepthPerThread = 4;
+// without it from the first step.  The bias factors 1 - beta^dt = -expm1(dt ln beta) are formed
+// once per block in FP32 (accurate to a few ulp, where 1 - beta^dt itself would cancel; an FP64
+// pow on one thread per block took most of the kernel's time on this GPU's FP64 pipe).
+constexpr int kDepthThreads = 128;  // nine blocks per SM at 55 registers
+constexpr int kDepthPerThread = 4;   // records per thread, independent (their loads overlap)
 constexpr int kDepthMaxPairs = 512;  // outgoing pairs of one view (the creation limit)
 
 template <int REC, int UPDATE>
 __global__ void __launch_bounds__(kDepthThreads) k_depth(StepArgs a, int chunks_per_view) {
-  __shared__ float s_w[kDepthMaxPairs];
-  __shared__ int64_t s_base[kDepthMaxPairs];
+  __shared__ float s_w[kDepthMaxPairs];       // the view's active pairs, in list order:
+  __shared__ int64_t s_base[kDepthMaxPairs];  // weight w_p / n_p and the pair's block of dzr
   __shared__ float s_c[2];
-  __shared__ int s_go;
+  __shared__ int s_go, s_n;
   const int v = blockIdx.x / chunks_per_view, ch = blockIdx.x % chunks_per_view;
+  const int lane = threadIdx.x & 31;
   const ViewDev vd = a.views[v];
-  if (threadIdx.x == 0) {
-    int go = 1;
-    if (UPDATE) {
-      go = !(*a.flag & 1);  // a refused step moves nothing
-      const int sc = vd.scene;
-      const int64_t s_cur = *a.step - 1;  // the step just taken
-      int64_t dt = s_cur + 1;
-      if (a.schedule) {
-        if (a.sched_state[2 * sc] != 2) go = 0;  // phase 1, or converged
-        dt = s_cur - a.sched_steps[2 * sc];
+  const int64_t r0 = vd.rec_begin, n = vd.n_rec;
+  const int64_t k0 = (int64_t)ch * kDepthThreads * kDepthPerThread + threadIdx.x;
+  if (threadIdx.x < 32) {
+    // warp 0: compact the view's active pairs (a fixed order: the view's pair list)
+    const int q0 = a.src_pair_off[v], nq = a.src_pair_off[v + 1] - q0;
+    int cnt = 0;
+    for (int k0 = 0; k0 < nq; k0 += 32) {
+      const int k = k0 + lane;
+      const int p = k < nq ? a.src_pair_ids[q0 + k] : 0;
+      const bool act = k < nq && a.pair_active[p];
+      const unsigned bal = __ballot_sync(0xffffffffu, act);
+      if (act) {  // the weight w_p / n_p from the pose kernel's loss blocks
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        s_w[pos] = a.pair_wz[p];
+        s_base[pos] = a.pp[p].dbase;
       }
-      if (dt < 1) go = 0;
-      if (go) {
-        s_c[0] = (float)(1.0 - pow(a.beta1, (double)dt));
-        s_c[1] = (float)(1.0 - pow(a.beta2, (double)dt));
+      cnt += __popc(bal);
+    }
+    if (lane == 0) {
+      s_n = cnt;
+      int go = 1;
+      if (UPDATE) {
+        go = !(*a.flag & 1);  // a refused step moves nothing
+        const int sc = vd.scene;
+        const int64_t s_cur = *a.step - 1;  // the step just taken
+        int64_t dt = s_cur + 1;
+        if (a.schedule) {
+          if (a.sched_state[2 * sc] != 2) go = 0;  // phase 1, or converged
+          dt = s_cur - a.sched_steps[2 * sc];
+        }
+        if (dt < 1) go = 0;
+        if (go) {
+          const float fdt = (float)dt;
+          s_c[0] = -expm1f(fdt * a.log_beta1);
+          s_c[1] = -expm1f(fdt * a.log_beta2);
+        }
       }
+      s_go = go;
     }
-    s_go = go;
-  }
-  const int q0 = a.src_pair_off[v], nq = a.src_pair_off[v + 1] - q0;
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int p = a.src_pair_ids[q0 + k];
-    float w = 0.f;
-    int64_t base = -1;
-    if (a.pair_active[p]) {
-      const double n = a.pair_acc[(size_t)kAcc * p + 1];
-      w = a.norm_all ? (float)a.pair_lw[p] : (n > 0.0 ? (float)(a.pair_lw[p] / n) : 0.f);
-      base = a.pp[p].dbase;
-    }
-    s_w[k] = w;
-    s_base[k] = base;
   }
   __syncthreads();
   if (!s_go) return;  // uniform over the block
-  const int64_t r0 = vd.rec_begin, n = vd.n_rec;
-  for (int64_t k = (int64_t)ch * kDepthThreads + threadIdx.x; k < n; k += (int64_t)chunks_per_view * kDepthThreads) {
+  const int np = s_n;
+  // dL/dz of the thread's records: eight pairs' loads for all of them in flight together,
+  // summed in the list order
+  float gz[kDepthPerThread];
+#pragma unroll
+  for (int j = 0; j < kDepthPerThread; ++j) gz[j] = 0.f;
+  constexpr int QB = 8;
+  for (int qb = 0; qb < np; qb += QB) {
+    float dv[QB][kDepthPerThread];
+#pragma unroll
+    for (int u = 0; u < QB; ++u) {
+      const bool qok = qb + u < np;
+      const float* d = a.dzr + (qok ? s_base[qb + u] : 0) + r0;
+#pragma unroll
+      for (int j = 0; j < kDepthPerThread; ++j) {
+        const int64_t k = k0 + j * kDepthThreads;
+        dv[u][j] = (qok && k < n) ? __ldg(d + k) : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QB; ++u) {
+      const float w = qb + u < np ? s_w[qb + u] : 0.f;
+#pragma unroll
+      for (int j = 0; j < kDepthPerThread; ++j) gz[j] = fmaf(w, dv[u][j], gz[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kDepthPerThread; ++j) {
+    const int64_t k = k0 + j * kDepthThreads;
+    if (k >= n) continue;
     const int64_t r = r0 + k;
-    float gz = 0.f;
-    for (int q = 0; q < nq; ++q)
-      if (s_base[q] >= 0) gz = fmaf(s_w[q], a.dzr[s_base[q] + r], gz);
     float u, w, z0;
     load_record<REC>(a.rec, r, u, w, z0);
-    const float ga = gz * z0;
+    const float gb = gz[j], ga = gb * z0;
     if (!UPDATE) {
       a.grad_alpha[r] = ga;
-      a.grad_beta[r] = gz;
+      a.grad_beta[r] = gb;
       continue;
     }
     const float c1 = s_c[0], c2 = s_c[1];
     const float b1 = (float)a.beta1, b2 = (float)a.beta2, lr = (float)a.lr_depth, eps = (float)a.adam_eps;
     const float ma = b1 * a.ma[r] + (1.f - b1) * ga, va = b2 * a.va[r] + (1.f - b2) * ga * ga;
-    const float mb = b1 * a.mb[r] + (1.f - b1) * gz, vb = b2 * a.vb[r] + (1.f - b2) * gz * gz;
+    const float mb = b1 * a.mb[r] + (1.f - b1) * gb, vb = b2 * a.vb[r] + (1.f - b2) * gb * gb;
     a.ma[r] = ma;
     a.va[r] = va;
     a.mb[r] = mb;

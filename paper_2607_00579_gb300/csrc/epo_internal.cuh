@@ -202,6 +202,7 @@ struct StepArgs {
   double lr_rot, lr_trans, beta1, beta2, adam_eps;
   // refinement optimiser (Algorithm 2 with the camera and depth modules)
   double lr_focal, lr_depth;
+  float log_beta1, log_beta2;        // ln beta1, ln beta2 (the depth module's bias factors)
   double* mg;                        // n_views Adam moments of gamma (f64)
   double* vg;
   float* alpha;                      // n_records: z = z0 alpha + beta
@@ -211,6 +212,8 @@ struct StepArgs {
   float* mb;
   float* vb;
   const float* dzr;                  // per (pair, record) d(rho)/dz of the fused pass
+  float* pair_wz;                    // n_pairs (refine scenes): w_p / n_p in f32, written by the
+                                     // pose kernel's loss blocks, read by the depth kernel
   const int32_t* src_pair_off;       // n_views + 1: the view's outgoing pairs in src_pair_ids
   const int32_t* src_pair_ids;
   float* grad_alpha;                 // n_records (gradient mode of the depth kernel)

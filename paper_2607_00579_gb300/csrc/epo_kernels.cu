@@ -350,14 +350,17 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     double acc = 0.0;
     if (p < range.y) {
       const double w = a.pair_lw[p];  // 0 for an inactive pair
+      double wn = 0.0;                // the weight of the pair's samples: w / n_p (w under Eq. 7)
       if (w != 0.0) {
         const double* pa = a.pair_acc + (size_t)kAcc * p;
         if (a.norm_all) {
-          acc = w * pa[0];
+          wn = w;
         } else if (pa[1] > 0.0) {
-          acc = w * pa[0] * __drcp_rn(pa[1]);
+          wn = w * __drcp_rn(pa[1]);
         }
+        acc = wn * pa[0];
       }
+      if (a.pair_wz) a.pair_wz[p] = (float)wn;  // refine scenes: read by the depth kernel
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
