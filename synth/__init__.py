@@ -369,3 +369,16 @@ def records_f16_widened(rec: np.ndarray) -> np.ndarray:
     out = rec.copy()
     out[:, 2] = rec[:, 2].astype(np.float16).astype(np.float32)
     return out
+
+
+def pose_mlp_init(seed: int = 20260100) -> np.ndarray:
+    """Initial parameters of the pose MLP (Section 3, Pose Refinement): Kaiming-normal weights
+    (std sqrt(2 / fan_in)) for the first five layers, the last layer zero, biases zero.  Flat
+    float32 in the layout W1 (128x12), b1, W2..W5 (128x128), b2..b5, W6 (12x128), b6."""
+    rng = np.random.default_rng(seed)
+    dims = [(128, 12), (128, 128), (128, 128), (128, 128), (128, 128), (12, 128)]
+    parts = []
+    for l, (o, i) in enumerate(dims):
+        W = np.zeros((o, i)) if l == 5 else rng.normal(0.0, np.sqrt(2.0 / i), (o, i))
+        parts += [W.ravel(), np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)
