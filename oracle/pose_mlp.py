@@ -10,6 +10,11 @@ added to the third's).  phi is Gram-Schmidt on the 6D representation of Zhou et 
 two columns of the 3x3 block); the translation passes through and delta_i is added.  The MLP
 is shared by the views of one scene; delta is per view.
 
+The parameterisation acts on the scene at unit scale (the paper's inputs are 3D foundation
+model outputs, which are normalised): with s the RMS distance of the P^0 camera centres from
+their centroid, the MLP sees P^0 with its translation divided by s, and its translation output
+and delta are multiplied by s.  P_i^s = [phi(R' ) | t_i^0 + s (y_t + delta_i)].
+
 Gradients come from the objective's left-perturbation gradient G_i = (g_v, g_w) of each pose
 (translation first), turned into Euclidean derivatives of the pose entries, then back through
 phi and the MLP.  AdamW (decoupled weight decay) with the learning-rate schedule of the paper:
@@ -117,16 +122,32 @@ def gram_schmidt_vjp(a1, a2, dR):
     return ga1, ga2
 
 
+def unit_scale(P0):
+    """RMS distance of the camera centres c = -R^T t from their centroid (1 if they coincide)."""
+    P = np.asarray(P0, dtype=np.float64).reshape(-1, 3, 4)
+    C = -np.einsum("vji,vj->vi", P[:, :, :3], P[:, :, 3])
+    s = float(np.sqrt(((C - C.mean(axis=0)) ** 2).sum(axis=1).mean()))
+    return s if s > 0.0 else 1.0
+
+
+def _tscale(s):
+    D = np.ones(12)
+    D[3::4] = s
+    return D
+
+
 def poses(theta, delta, P0):
     """P^s (n, 12) of Eq. 3 and the cache for pose_backward."""
     P0 = np.asarray(P0, dtype=np.float64).reshape(-1, 12)
-    y, cache = mlp_forward(theta, P0)
-    Pp = (P0 + y).reshape(-1, 3, 4)
+    s = unit_scale(P0)
+    D = _tscale(s)
+    y, cache = mlp_forward(theta, P0 / D)
+    Pp = (P0 + D * y).reshape(-1, 3, 4)
     out = np.zeros((len(P0), 3, 4))
     for v in range(len(P0)):
         out[v, :, :3] = gram_schmidt(Pp[v, :, 0], Pp[v, :, 1])
-        out[v, :, 3] = Pp[v, :, 3] + delta[v]
-    return out.reshape(-1, 12), (cache, Pp)
+        out[v, :, 3] = Pp[v, :, 3] + s * np.asarray(delta[v])
+    return out.reshape(-1, 12), (cache, Pp, s)
 
 
 def euclidean_pose_grad(T, G):
@@ -148,16 +169,16 @@ def euclidean_pose_grad(T, G):
 
 def pose_backward(theta, cache, T, G):
     """dL/dtheta and dL/ddelta from the left-perturbation gradient G at the poses T = P^s."""
-    mcache, Pp = cache
+    mcache, Pp, s = cache
     dR, dt = euclidean_pose_grad(T, G)
     dy = np.zeros((len(Pp), 3, 4))
     for v in range(len(Pp)):
         ga1, ga2 = gram_schmidt_vjp(Pp[v, :, 0], Pp[v, :, 1], dR[v])
         dy[v, :, 0] = ga1
         dy[v, :, 1] = ga2
-        dy[v, :, 3] = dt[v]
+        dy[v, :, 3] = s * dt[v]
     gtheta, _ = mlp_backward(theta, mcache, dy.reshape(-1, 12))
-    return gtheta, dt.copy()
+    return gtheta, s * dt
 
 
 def lr_at(step, lr_max=3e-3, warmup=25, total=2000):

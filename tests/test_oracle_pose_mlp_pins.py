@@ -145,3 +145,21 @@ def test_pose_mlp_run_descends(ring8):
     f = lambda T: (lambda r: (r["loss"], r["grad"]))(o.loss_grad(T, lam=10.0))
     losses = [run.step_with(f)[0] for _ in range(40)]
     assert losses[-1] < 0.8 * losses[0]
+
+
+def test_parameterisation_acts_on_the_unit_scale_scene():
+    """Scaling the scene's translations by k scales the parameterised translations by k and
+    leaves the rotations: the MLP sees (and moves) the scene at unit scale."""
+    sc = synth.make_scene(synth.RING8_128x96)
+    rng = np.random.default_rng(9)
+    theta = synth.pose_mlp_init(10).astype(np.float64)
+    theta[-(12 * 128 + 12):] = rng.normal(0, 1e-2, 12 * 128 + 12)
+    delta = rng.normal(0, 0.01, (sc.n_views, 3))
+    P0 = np.asarray(sc.T_init).reshape(-1, 3, 4)
+    T1 = pm.poses(theta, delta, P0)[0].reshape(-1, 3, 4)
+    P0k = P0.copy()
+    P0k[:, :, 3] *= 7.0
+    T2 = pm.poses(theta, delta, P0k)[0].reshape(-1, 3, 4)
+    assert np.allclose(T2[:, :, :3], T1[:, :, :3], atol=1e-13)
+    assert np.allclose(T2[:, :, 3], 7.0 * T1[:, :, 3], rtol=1e-12, atol=1e-12)
+    assert pm.unit_scale(P0k) == pytest.approx(7.0 * pm.unit_scale(P0), rel=1e-12)
