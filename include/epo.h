@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define EPO_ABI_VERSION 3
+#define EPO_ABI_VERSION 4
 
 typedef enum {
   EPO_OK = 0,
@@ -60,6 +60,11 @@ typedef enum {
 } epo_status;
 
 enum { EPO_F32 = 0, EPO_F16 = 1, EPO_BF16 = 2 };
+/* Pose parameterisation: direct SE(3) parameters or the paper's pose MLP (Eq. 3). */
+enum { EPO_POSE_SE3 = 0, EPO_POSE_MLP = 1 };
+/* Parameters of one scene's pose MLP (12 -> 128 x 5 -> 12), in the order W1 (128x12, row-major
+ * [out][in]), b1, W2..W5 (128x128), b2..b5, W6 (12x128), b6. */
+#define EPO_POSE_MLP_PARAMS 69260
 /* Per-direction normaliser: sum(valid) (Algorithm 3) or |E_i| (Eq. 7). */
 enum { EPO_NORM_VALID = 0, EPO_NORM_ALL = 1 };
 /* How the kernels read the 2x2 map footprint: plain loads or texture gather. */
@@ -137,6 +142,17 @@ typedef struct {
                                 module steps only in phase 2 of the schedule (Algorithm 2) when
                                 options.schedule is on, else from the first step; its Adam bias
                                 correction counts its own steps.  0 (default) keeps alpha, beta */
+  int32_t pose_param;        /* EPO_POSE_SE3 (default): each pose is its own parameter, Adam in
+                                the tangent space; EPO_POSE_MLP: the paper's parameterisation
+                                (Section 3, Pose Refinement, Eq. 3), P_i = phi(P_i^0 + MLP(P_i^0))
+                                + [0 | delta_i] with one MLP per scene (set by epo_set_pose_mlp)
+                                and AdamW; every view moves (fixed is not used) */
+  double mlp_lr;             /* peak learning rate of the MLP and delta (default 3e-3) */
+  int32_t mlp_warmup;        /* linear warm-up steps (default 25): step s < warmup uses
+                                (s + 1) / warmup of mlp_lr */
+  int32_t mlp_steps;         /* then cosine decay, reaching 0 at step mlp_steps - 1 (default 2000) */
+  double mlp_wd, mlp_wd_delta; /* AdamW weight decay of the MLP and of delta (0.01, 0.1) */
+  double mlp_eps;            /* AdamW epsilon (default 1e-8) */
 } epo_options;
 
 /* Per-scene facts, filled by epo_scene_info. */
@@ -268,6 +284,24 @@ epo_status epo_stage_times(epo_scene_t scene, float* ms);
  * (options.lr_focal, lr_depth).  Synchronises.  EPO_ERR_INVALID_ARG on a scene
  * without refinement or non-finite values. */
 epo_status epo_set_refinement(epo_scene_t scene, const double* gamma, const float* alpha, const float* beta);
+
+/* Parameters of the pose MLP (options.pose_param = EPO_POSE_MLP; Section 3, Pose Refinement):
+ * params holds n_scenes x EPO_POSE_MLP_PARAMS floats (host; the initialisation is the caller's,
+ * e.g. Kaiming-normal layers with the last layer zero).  Clears the AdamW moments and the
+ * offsets delta, keeps the initial poses P^0 (those of the last epo_set_poses) and sets the
+ * current poses to P^s of the new parameters.  Synchronises.  EPO_ERR_INVALID_ARG on a scene
+ * in SE(3) mode or non-finite values.  In MLP mode epo_set_poses sets P^0, clears delta and
+ * recomputes the poses from the current parameters (all zero until this call: P^s = P^0). */
+epo_status epo_set_pose_mlp(epo_scene_t scene, const float* params);
+
+/* The current MLP parameters (n_scenes x EPO_POSE_MLP_PARAMS floats) and offsets (n_views x 3
+ * floats); either may be NULL.  Host outputs.  Synchronises. */
+epo_status epo_get_pose_mlp(epo_scene_t scene, float* params, float* delta);
+
+/* The AdamW moments of the pose MLP: m and v of the parameters (n_scenes x
+ * EPO_POSE_MLP_PARAMS floats each) and of the offsets (n_views x 3 each); any may be NULL.
+ * Host outputs.  Synchronises. */
+epo_status epo_get_pose_mlp_moments(epo_scene_t scene, float* m, float* v, float* dm, float* dv);
 
 /* The current refinement (after the steps that updated it): gamma (n_views
  * doubles), alpha and beta (n_records floats each).  Host outputs, any may be

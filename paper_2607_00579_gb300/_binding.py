@@ -40,6 +40,7 @@ EXPORTED = [
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
     "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph", "epo_get_refinement",
+    "epo_set_pose_mlp", "epo_get_pose_mlp", "epo_get_pose_mlp_moments",
 ]
 
 
@@ -74,7 +75,10 @@ class epo_options(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("pair_budget", ctypes.c_int32),
                 ("subsample_seed", ctypes.c_uint64), ("sched_eps1", ctypes.c_double),
                 ("sched_eps2", ctypes.c_double), ("schedule", ctypes.c_int32), ("sched_w1", ctypes.c_int32),
-                ("sched_w2", ctypes.c_int32), ("lr_focal", ctypes.c_double), ("lr_depth", ctypes.c_double)]
+                ("sched_w2", ctypes.c_int32), ("lr_focal", ctypes.c_double), ("lr_depth", ctypes.c_double),
+                ("pose_param", ctypes.c_int32), ("mlp_lr", ctypes.c_double), ("mlp_warmup", ctypes.c_int32),
+                ("mlp_steps", ctypes.c_int32), ("mlp_wd", ctypes.c_double), ("mlp_wd_delta", ctypes.c_double),
+                ("mlp_eps", ctypes.c_double)]
 
 
 class epo_scene_info(ctypes.Structure):
@@ -303,6 +307,36 @@ def epo_set_refinement(scene, gamma=None, alpha=None, beta=None):
     a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float32)
     b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float32)
     _call("epo_set_refinement", scene, _ptr(g), _ptr(a), _ptr(b))
+
+
+EPO_POSE_SE3, EPO_POSE_MLP = 0, 1
+EPO_POSE_MLP_PARAMS = 69260
+
+
+def epo_set_pose_mlp(scene, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _call("epo_set_pose_mlp", scene, _ptr(p))
+
+
+def epo_get_pose_mlp(scene, n_scenes: int, n_views: int):
+    """Returns (params (n_scenes, EPO_POSE_MLP_PARAMS) float32, delta (n_views, 3) float32)."""
+    import numpy as np
+    p = np.zeros((n_scenes, EPO_POSE_MLP_PARAMS), np.float32)
+    d = np.zeros((n_views, 3), np.float32)
+    _call("epo_get_pose_mlp", scene, _ptr(p), _ptr(d))
+    return p, d
+
+
+def epo_get_pose_mlp_moments(scene, n_scenes: int, n_views: int):
+    """Returns (m, v (n_scenes, EPO_POSE_MLP_PARAMS), dm, dv (n_views, 3)), float32."""
+    import numpy as np
+    m = np.zeros((n_scenes, EPO_POSE_MLP_PARAMS), np.float32)
+    v = np.zeros_like(m)
+    dm = np.zeros((n_views, 3), np.float32)
+    dv = np.zeros_like(dm)
+    _call("epo_get_pose_mlp_moments", scene, _ptr(m), _ptr(v), _ptr(dm), _ptr(dv))
+    return m, v, dm, dv
 
 
 def epo_get_refinement(scene, n_views: int, n_records: int):

@@ -67,6 +67,7 @@ struct epo_scene {
   std::vector<ViewDev> views;
   std::vector<int32_t> pair_src, pair_dst, pair_scene, scene_pair_off, scene_active;
   std::vector<int32_t> src_pair_off, src_pair_ids;
+  std::vector<int32_t> scene_view_begin;  // n_scenes + 1: the views of each scene (contiguous)
   std::vector<uint8_t> active;
   // device buffers
   std::vector<DevBuf> bufs;
@@ -130,6 +131,13 @@ struct epo_scene {
   double *d_mg = nullptr, *d_vg = nullptr;
   float *d_ma = nullptr, *d_va = nullptr, *d_mb = nullptr, *d_vb = nullptr;
   int depth_opt = 0;           // refine && lr_depth > 0: the depth module's kernel in every step
+  // pose MLP (options.pose_param = EPO_POSE_MLP)
+  int pose_mlp = 0;
+  float *d_mlp_theta = nullptr, *d_mlp_m = nullptr, *d_mlp_v = nullptr, *d_mlp_delta = nullptr,
+        *d_mlp_dm = nullptr, *d_mlp_dv = nullptr, *d_mlp_gdelta = nullptr, *d_mlp_x = nullptr,
+        *d_mlp_z = nullptr, *d_mlp_dz = nullptr;
+  double *d_mlp_P0 = nullptr, *d_mlp_Pp = nullptr, *d_mlp_scale = nullptr;
+  unsigned int* d_mlp_done = nullptr;
   int32_t max_view_records = 0;
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
@@ -310,6 +318,27 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.rec = S->d_rec;
   a.rec_dtype = S->rec_dtype;
   a.max_view_records = S->max_view_records;
+  a.pose_mlp = S->pose_mlp;
+  a.mlp_theta = S->d_mlp_theta;
+  a.mlp_m = S->d_mlp_m;
+  a.mlp_v = S->d_mlp_v;
+  a.mlp_P0 = S->d_mlp_P0;
+  a.mlp_scale = S->d_mlp_scale;
+  a.mlp_Pp = S->d_mlp_Pp;
+  a.mlp_delta = S->d_mlp_delta;
+  a.mlp_dm = S->d_mlp_dm;
+  a.mlp_dv = S->d_mlp_dv;
+  a.mlp_gdelta = S->d_mlp_gdelta;
+  a.mlp_x = S->d_mlp_x;
+  a.mlp_z = S->d_mlp_z;
+  a.mlp_dz = S->d_mlp_dz;
+  a.mlp_done = S->d_mlp_done;
+  a.mlp_lr = (float)S->opt.mlp_lr;
+  a.mlp_warmup = S->opt.mlp_warmup;
+  a.mlp_steps = S->opt.mlp_steps;
+  a.mlp_wd = (float)S->opt.mlp_wd;
+  a.mlp_wd_delta = (float)S->opt.mlp_wd_delta;
+  a.mlp_eps = (float)S->opt.mlp_eps;
   return a;
 }
 
@@ -502,7 +531,12 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   epo_status st = run_edge(S, MODE_FUSED, S->gather, S->rpt, S->block, S->tail, s);
   if (st != EPO_OK) return st;
   CK(launch_poses(a, 2, s));
+  if (S->pose_mlp) {  // the poses' gradient through phi and the MLP; AdamW (advances the step)
+    CK(launch_mlp_backward(a, s));
+    CK(launch_mlp_update(a, s));
+  }
   if (S->depth_opt) CK(launch_depth(a, 1, s));
+  if (S->pose_mlp) CK(launch_mlp_forward(a, 1, s));  // the next poses and their change
   if (S->opt.schedule) CK(launch_schedule(a, s));
   MARK(3, s);
   return EPO_OK;
@@ -567,8 +601,15 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "lr_focal and lr_depth must be finite and >= 0");
   if (!o.refine && (o.lr_focal != 0 || o.lr_depth != 0))
     return fail(nullptr, EPO_ERR_INVALID_ARG, "lr_focal and lr_depth need options.refine = 1");
+  if (o.pose_param != EPO_POSE_SE3 && o.pose_param != EPO_POSE_MLP)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown pose_param");
+  if (o.pose_param == EPO_POSE_MLP &&
+      (!(o.mlp_lr >= 0) || !isfinite(o.mlp_lr) || o.mlp_warmup < 0 || o.mlp_steps < 1 || !(o.mlp_wd >= 0) ||
+       !(o.mlp_wd_delta >= 0) || !(o.mlp_eps > 0)))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "pose MLP: lr, decays >= 0, warmup >= 0, steps >= 1, eps > 0");
   S->refine = o.refine;
   S->depth_opt = o.refine && o.lr_depth > 0;
+  S->pose_mlp = o.pose_param == EPO_POSE_MLP;
   S->stream = (cudaStream_t)cuda_stream;
   const int rec_dtype = descs[0].record_dtype, map_dtype = descs[0].map_dtype;
   if (rec_dtype != EPO_F32 && rec_dtype != EPO_F16) return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown record dtype");
@@ -783,27 +824,54 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_pair_ij, np);
     ALLOC(S->d_pair_lw, np);
     ALLOC(S->d_pose_entries, (size_t)nv * S->pose_stride);
-    if (o.schedule) {
+    S->scene_view_begin.assign(1, 0);
+    for (int sc = 0; sc < n_scenes; ++sc) S->scene_view_begin.push_back(S->scene_view_begin.back() + descs[sc].n_views);
+    if (o.schedule || o.pose_param == EPO_POSE_MLP) {  // views of each scene (contiguous)
       ALLOC(S->d_scene_view_off, n_scenes + 1);
+      CK(cudaMemcpy(S->d_scene_view_off, S->scene_view_begin.data(), (n_scenes + 1) * 4, cudaMemcpyHostToDevice));
+    }
+    if (o.schedule) {
       ALLOC(S->d_pose_dR, nv);
       ALLOC(S->d_pose_dt, nv);
       ALLOC(S->d_sched_state, 2 * (size_t)n_scenes);
       ALLOC(S->d_theta95, n_scenes);
       ALLOC(S->d_sched_steps, 2 * (size_t)n_scenes);
-      std::vector<int32_t> vo(1, 0), ss(2 * (size_t)n_scenes);
+      std::vector<int32_t> ss(2 * (size_t)n_scenes);
       for (int sc = 0; sc < n_scenes; ++sc) {
-        vo.push_back(vo.back() + descs[sc].n_views);
         ss[2 * sc] = 1;
         ss[2 * sc + 1] = 0;
       }
       std::vector<int64_t> steps(2 * (size_t)n_scenes, -1);
       std::vector<double> th(n_scenes, 0.0);
-      CK(cudaMemcpy(S->d_scene_view_off, vo.data(), vo.size() * 4, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(S->d_sched_state, ss.data(), ss.size() * 4, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(S->d_sched_steps, steps.data(), steps.size() * 8, cudaMemcpyHostToDevice));
       CK(cudaMemcpy(S->d_theta95, th.data(), th.size() * 8, cudaMemcpyHostToDevice));
       CK(cudaMemset(S->d_pose_dR, 0, (size_t)nv * 8));
       CK(cudaMemset(S->d_pose_dt, 0, (size_t)nv * 8));
+    }
+    if (S->pose_mlp) {
+      const size_t np_ = (size_t)n_scenes * kMlpParams;
+      ALLOC(S->d_mlp_theta, np_);
+      ALLOC(S->d_mlp_m, np_);
+      ALLOC(S->d_mlp_v, np_);
+      ALLOC(S->d_mlp_P0, 12 * (size_t)nv);
+      ALLOC(S->d_mlp_Pp, 12 * (size_t)nv);
+      ALLOC(S->d_mlp_delta, 3 * (size_t)nv);
+      ALLOC(S->d_mlp_dm, 3 * (size_t)nv);
+      ALLOC(S->d_mlp_dv, 3 * (size_t)nv);
+      ALLOC(S->d_mlp_gdelta, 3 * (size_t)nv);
+      ALLOC(S->d_mlp_x, 12 * (size_t)nv);
+      ALLOC(S->d_mlp_z, 5 * (size_t)kMlpHid * nv);
+      ALLOC(S->d_mlp_dz, (size_t)kMlpDz * nv);
+      ALLOC(S->d_mlp_done, 1);
+      ALLOC(S->d_mlp_scale, n_scenes);
+      {
+        std::vector<double> one(n_scenes, 1.0);  // identity poses: the centres coincide
+        CK(cudaMemcpy(S->d_mlp_scale, one.data(), one.size() * 8, cudaMemcpyHostToDevice));
+      }
+      for (float* q : {S->d_mlp_theta, S->d_mlp_m, S->d_mlp_v}) CK(cudaMemset(q, 0, np_ * 4));
+      for (float* q : {S->d_mlp_delta, S->d_mlp_dm, S->d_mlp_dv, S->d_mlp_gdelta}) CK(cudaMemset(q, 0, 12 * (size_t)nv));
+      CK(cudaMemset(S->d_mlp_done, 0, 4));
     }
     if (S->refine) {
       ALLOC(S->d_gamma, nv);
@@ -856,6 +924,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     std::vector<double> I(12 * (size_t)nv, 0.0);
     for (int v = 0; v < nv; ++v) I[12 * v] = I[12 * v + 5] = I[12 * v + 10] = 1.0;
     CK(cudaMemcpyAsync(S->d_T, I.data(), I.size() * 8, cudaMemcpyHostToDevice, st));
+    if (S->pose_mlp) CK(cudaMemcpyAsync(S->d_mlp_P0, I.data(), I.size() * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(S->d_m, 0, 6 * (size_t)nv * 8, st));
     CK(cudaMemsetAsync(S->d_v, 0, 6 * (size_t)nv * 8, st));
     {
@@ -897,6 +966,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       if (rs != EPO_OK) return rs;
       CK(cudaMemsetAsync(S->d_pair_facc, 0, (size_t)2 * np * 8, st));
     }
+    if (S->pose_mlp) CK(launch_mlp_forward(step_args(S, S->d_T, nullptr), 0, st));  // zero MLP: P^s = P^0
     // validate maps on the device
     CK(launch_map_check(S->d_map, S->map_dtype, S->map_elems, S->d_flag, st));
     CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, st));
@@ -1023,6 +1093,13 @@ void epo_default_options(epo_options* o) {
   o->sched_eps2 = 0.1;
   o->sched_w1 = 25;
   o->sched_w2 = 50;
+  o->pose_param = EPO_POSE_SE3;
+  o->mlp_lr = 3e-3;  // Section 3, Implementation Details
+  o->mlp_warmup = 25;
+  o->mlp_steps = 2000;
+  o->mlp_wd = 0.01;
+  o->mlp_wd_delta = 0.1;
+  o->mlp_eps = 1e-8;
 }
 
 int32_t epo_abi_version(void) { return EPO_ABI_VERSION; }
@@ -1084,8 +1161,32 @@ epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
   info->block_threads = S->block;
   info->records_per_thread = S->rpt;
   info->grid_blocks = grid_for(S, S->gather, S->rpt, S->block);
-  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule + S->depth_opt;
+  info->kernels_per_step = 3 + S->refine + S->subsample + S->opt.schedule + S->depth_opt + 3 * S->pose_mlp;
   info->tail_pairs = S->tail;
+  return EPO_OK;
+}
+
+// Per scene the RMS distance of the camera centres c = -R^T t of the poses T from their
+// centroid (1 if they coincide): the pose MLP acts on the scene at this unit scale.
+static epo_status set_mlp_scale(epo_scene* S, const double* T) {
+  std::vector<double> sc(S->n_scenes, 1.0);
+  for (int s = 0; s < S->n_scenes; ++s) {
+    const int v0 = S->scene_view_begin[s], v1 = S->scene_view_begin[s + 1];
+    double mean[3] = {0, 0, 0}, acc = 0.0;
+    std::vector<double> C(3 * (size_t)(v1 - v0));
+    for (int v = v0; v < v1; ++v) {
+      const double* P = T + 12 * (size_t)v;
+      for (int k = 0; k < 3; ++k) {
+        C[3 * (v - v0) + k] = -(P[k] * P[3] + P[4 + k] * P[7] + P[8 + k] * P[11]);
+        mean[k] += C[3 * (v - v0) + k] / (v1 - v0);
+      }
+    }
+    for (int v = 0; v < v1 - v0; ++v)
+      for (int k = 0; k < 3; ++k) acc += (C[3 * v + k] - mean[k]) * (C[3 * v + k] - mean[k]);
+    const double r = v1 > v0 ? sqrt(acc / (v1 - v0)) : 0.0;
+    sc[s] = r > 0.0 ? r : 1.0;
+  }
+  CK(cudaMemcpyAsync(S->d_mlp_scale, sc.data(), sc.size() * 8, cudaMemcpyHostToDevice, S->stream));
   return EPO_OK;
 }
 
@@ -1094,6 +1195,51 @@ epo_status epo_set_poses(epo_scene_t S, const double* T) {
   for (int64_t k = 0; k < 12 * (int64_t)S->n_views; ++k)
     if (!isfinite(T[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
   CK(cudaMemcpyAsync(S->d_T, T, 12 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
+  if (S->pose_mlp) {  // the MLP's input P^0; the offsets restart at 0; the poses follow
+    const size_t nv = (size_t)S->n_views;
+    epo_status st = set_mlp_scale(S, T);
+    if (st != EPO_OK) return st;
+    CK(cudaMemcpyAsync(S->d_mlp_P0, T, 12 * nv * 8, cudaMemcpyHostToDevice, S->stream));
+    for (float* q : {S->d_mlp_delta, S->d_mlp_dm, S->d_mlp_dv}) CK(cudaMemsetAsync(q, 0, 12 * nv, S->stream));
+    CK(launch_mlp_forward(step_args(S, S->d_T, nullptr), 0, S->stream));
+  }
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_set_pose_mlp(epo_scene_t S, const float* params) {
+  if (!S || !params) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
+  if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
+  const size_t n = (size_t)S->n_scenes * kMlpParams, nv = (size_t)S->n_views;
+  for (size_t k = 0; k < n; ++k)
+    if (!isfinite(params[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite MLP parameter");
+  CK(cudaMemcpyAsync(S->d_mlp_theta, params, n * 4, cudaMemcpyHostToDevice, S->stream));
+  CK(cudaMemsetAsync(S->d_mlp_m, 0, n * 4, S->stream));
+  CK(cudaMemsetAsync(S->d_mlp_v, 0, n * 4, S->stream));
+  for (float* q : {S->d_mlp_delta, S->d_mlp_dm, S->d_mlp_dv}) CK(cudaMemsetAsync(q, 0, 12 * nv, S->stream));
+  CK(launch_mlp_forward(step_args(S, S->d_T, nullptr), 0, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_pose_mlp_moments(epo_scene_t S, float* m, float* v, float* dm, float* dv) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
+  const size_t n = (size_t)S->n_scenes * kMlpParams * 4, nd = 12 * (size_t)S->n_views;
+  if (m) CK(cudaMemcpyAsync(m, S->d_mlp_m, n, cudaMemcpyDeviceToHost, S->stream));
+  if (v) CK(cudaMemcpyAsync(v, S->d_mlp_v, n, cudaMemcpyDeviceToHost, S->stream));
+  if (dm) CK(cudaMemcpyAsync(dm, S->d_mlp_dm, nd, cudaMemcpyDeviceToHost, S->stream));
+  if (dv) CK(cudaMemcpyAsync(dv, S->d_mlp_dv, nd, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_get_pose_mlp(epo_scene_t S, float* params, float* delta) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
+  if (params)
+    CK(cudaMemcpyAsync(params, S->d_mlp_theta, (size_t)S->n_scenes * kMlpParams * 4, cudaMemcpyDeviceToHost, S->stream));
+  if (delta) CK(cudaMemcpyAsync(delta, S->d_mlp_delta, 12 * (size_t)S->n_views, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   return EPO_OK;
 }
@@ -1108,6 +1254,17 @@ epo_status epo_get_poses(epo_scene_t S, double* T) {
 epo_status epo_set_poses_dev(epo_scene_t S, const double* T) {
   if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(S->d_T, T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
+  if (S->pose_mlp) {  // as epo_set_poses: P^0, offsets cleared, poses recomputed
+    const size_t nv = (size_t)S->n_views;
+    std::vector<double> Th(12 * nv);
+    CK(cudaMemcpyAsync(Th.data(), T, 12 * nv * 8, cudaMemcpyDeviceToHost, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+    epo_status st = set_mlp_scale(S, Th.data());
+    if (st != EPO_OK) return st;
+    CK(cudaMemcpyAsync(S->d_mlp_P0, T, 12 * nv * 8, cudaMemcpyDeviceToDevice, S->stream));
+    for (float* q : {S->d_mlp_delta, S->d_mlp_dm, S->d_mlp_dv}) CK(cudaMemsetAsync(q, 0, 12 * nv, S->stream));
+    CK(launch_mlp_forward(step_args(S, S->d_T, nullptr), 0, S->stream));
+  }
   return EPO_OK;
 }
 

@@ -221,13 +221,45 @@ struct StepArgs {
   const void* rec;                   // records (z0)
   int32_t rec_dtype;
   int32_t max_view_records;          // most records of one view (grid of the depth update)
+  // pose parameterisation (Section 3, Pose Refinement, Eq. 3): P^s = phi(P^0 + MLP(P^0)) +
+  // [0 | delta]; the pose kernel then only forms the gradient (and gamma's step)
+  int32_t pose_mlp;
+  float* mlp_theta;                  // n_scenes x kMlpParams (layout of kMlpDims)
+  float* mlp_m;                      // AdamW moments of theta
+  float* mlp_v;
+  const double* mlp_P0;              // n_views x 12: the initial poses (the MLP's input)
+  const double* mlp_scale;           // n_scenes: RMS spread of the P^0 camera centres (the MLP acts
+                                     // on the scene at unit scale: translations / s in, x s out)
+  double* mlp_Pp;                    // n_views x 12: P^0 + MLP(P^0) of the current poses
+  float* mlp_delta;                  // n_views x 3 translation offsets, their moments and gradient
+  float* mlp_dm;
+  float* mlp_dv;
+  float* mlp_gdelta;
+  float* mlp_x;                      // n_views x 12: the input as the MLP saw it (f32)
+  float* mlp_z;                      // n_views x 5 x 128: pre-activations of the hidden layers
+  float* mlp_dz;                     // n_views x (5 x 128 + 12): dL/dz of every layer
+  unsigned int* mlp_done;            // completion counter of the update kernel
+  float mlp_lr;                      // peak learning rate
+  int32_t mlp_warmup, mlp_steps;     // linear warm-up steps; the cosine reaches 0 at mlp_steps - 1
+  float mlp_wd, mlp_wd_delta, mlp_eps;
 };
+
+// Pose MLP: 12 -> 128 -> 128 -> 128 -> 128 -> 128 -> 12; parameters per scene in the order
+// W1 (128x12, row-major [out][in]), b1, W2..W5 (128x128), b2..b5, W6 (12x128), b6.
+constexpr int kMlpHid = 128;
+constexpr int kMlpParams = kMlpHid * 12 + kMlpHid + 4 * (kMlpHid * kMlpHid + kMlpHid) + 12 * kMlpHid + 12;
+constexpr int kMlpDz = 5 * kMlpHid + 12;  // per view: dL/dz of the five hidden layers and the output
 
 // ---- launchers (epo_kernels.cu) ----
 cudaError_t launch_pair_setup(const StepArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_refine_intrinsics(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_subsample(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_schedule(const StepArgs& a, cudaStream_t s);
+// pose MLP (epo_pose_mlp.cu): forward (new poses; change = 1 also records the pose changes of
+// the step), backward through phi and the MLP, AdamW update of theta and delta
+cudaError_t launch_mlp_forward(const StepArgs& a, int change, cudaStream_t s);
+cudaError_t launch_mlp_backward(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_mlp_update(const StepArgs& a, cudaStream_t s);
 // depth kernel: update 0 = dL/dalpha, dL/dbeta into grad_alpha, grad_beta; 1 = Adam step
 cudaError_t launch_depth(const StepArgs& a, int update, cudaStream_t s);
 cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms, cudaStream_t s);

@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     if (with_grad == 2) {
       const bool bad = vv && e < 6 && !isfinite(G);
       const unsigned badmask = __ballot_sync(0xffffffffu, bad);
-      const bool skip = !vv || (flag0 & 1) || a.fixed[v] || conv || ((badmask >> base) & 0xffffu);
+      // under the pose MLP the poses come from its forward kernel: only the gradient is formed
+      const bool skip = !vv || (flag0 & 1) || a.fixed[v] || conv || a.pose_mlp || ((badmask >> base) & 0xffffu);
       double xi = 0.0;
       if (!skip && e < 6) {
         const size_t o = 6 * (size_t)v + e;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       if (!skip && e < 12) Tnew = fma(E0, Tc0, fma(E1, Tc1, fma(E2, Tc2, c == 3 ? E3 : 0.0)));
       __syncwarp();  // every lane has read the old pose before any lane writes it
       if (!skip && e < 12) a.T_store[12 * (size_t)v + e] = Tnew;
-      if (a.schedule) {
+      if (a.schedule && !a.pose_mlp) {
         // the step's pose change (Section 3, Optimization Schedule): lane (r, c) holds entry
         // (r, c) of the old and the new pose; tr(R_new R_old^T) and the translations' dot
         // product and norms are reduced over the pose's 16 lanes in a fixed order
@@ -386,8 +387,9 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       }
     }
   }
-  if (with_grad == 2) {
-    // the last block to finish advances the step counter and the beta powers
+  if (with_grad == 2 && !a.pose_mlp) {
+    // the last block to finish advances the step counter and the beta powers (under the pose
+    // MLP its update kernel does)
     __syncwarp();
     if (threadIdx.x == 0) {
       __threadfence();

@@ -28,7 +28,7 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 
 def test_abi_version_and_defaults():
-    assert epo._binding.epo_abi_version() == 3
+    assert epo._binding.epo_abi_version() == 4
     o = epo.default_options()
     assert o.huber_delta == 1.0 and o.lambda0 == 10.0 and o.lambda1 == 6.0 and o.lambda_steps == 1000
     assert o.beta1 == 0.9 and o.beta2 == 0.999 and o.norm_mode == epo.EPO_NORM_VALID
