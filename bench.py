@@ -490,6 +490,8 @@ def run_ours(args):
     elif wl.key == "ring32":
         line["refine"] = refine_leg(epo, torch, wl, parts, (rd, md), lr, evals, args, flush_l2, stream, sched)
         line["viewgraph"] = viewgraph_leg(epo, torch, wl)
+        line["pose_mlp"] = pose_mlp_leg(epo, torch, wl, parts, (rd, md), lr, evals, args, flush_l2, stream,
+                                        {k: v for k, v in sched.items()})
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -597,6 +599,27 @@ def refine_leg(epo, torch, wl, parts, dtypes, lr, evals, args, flush_l2, stream,
             "d2h_bytes_per_evaluation": int(8 * info.n_scenes + 56 * info.n_views + 8 * info.n_records),
             "note": "wall time of epo_refine_loss_and_grad (fused pass, depth kernel, host copies of all gradients)",
             "step": step}
+
+
+def pose_mlp_leg(epo, torch, wl, parts, dtypes, lr, evals, args, flush_l2, stream, sched):
+    """The paper's pose parameterisation (Eq. 3: one MLP per scene, Gram-Schmidt, translation
+    offsets, AdamW with warm-up and cosine decay) as graph steps: the fused pass, the pose
+    kernel's gradient, the MLP's backward, AdamW and forward."""
+    import synth
+    B = epo._binding
+    h = epo.Scene(parts, record_dtype=dtypes[0], map_dtype=dtypes[1], on_device=True,
+                  options=epo.default_options(pose_param=B.EPO_POSE_MLP, **lr, **sched))
+    h.set_poses(wl.T_init)
+    B.epo_set_pose_mlp(h.handle, np.concatenate([synth.pose_mlp_init(20260100 + k) for k in range(h.info().n_scenes)]))
+    for _ in range(3):
+        h.step_async(1)
+    torch.cuda.synchronize()
+    n = max(5, min(args.steps, 50))
+    ms = float(np.mean(time_steps(h, n, flush_l2, stream, torch)))
+    return {"value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "iterations": n,
+            "kernels_per_step": int(h.info().kernels_per_step),
+            "note": "graph steps of the MLP parameterisation (per-scene MLP 12-128x5-12 in FP32, "
+                    "Gram-Schmidt and poses in FP64), Kaiming-initialised, inside the warm-up"}
 
 
 def autograd_leg(epo, torch, s, T_init, evals, args, flush_l2, stream):
