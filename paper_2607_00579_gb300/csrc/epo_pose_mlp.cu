@@ -42,6 +42,14 @@ __host__ __device__ constexpr int mlp_w(int l) {
 __host__ __device__ constexpr int mlp_b(int l) { return mlp_w(l) + mlp_out(l) * mlp_in(l); }
 static_assert(mlp_w(6) == kMlpParams, "pose MLP layout");
 
+// Every block starts the scene's weights (280 KB) towards L2 at once: the layers then wait on
+// L2 rather than on one DRAM round trip after another (each step starts with them cold).
+__device__ __forceinline__ void prefetch_weights(const float* th) {
+  constexpr int kLines = (kMlpParams * 4 + 127) / 128;
+  for (int q = threadIdx.x; q < kLines; q += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(th) + (size_t)q * 128));
+}
+
 __device__ __forceinline__ double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -58,6 +66,7 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_forward(StepArgs a, int change)
   const int v = blockIdx.x, j = threadIdx.x;
   const int sc = a.views[v].scene;
   const float* th = a.mlp_theta + (size_t)sc * kMlpParams;
+  prefetch_weights(th);
   __shared__ float s_x[12], s_a[H], s_a1[H], s_y[12];
   const double sc_s = a.mlp_scale[sc];
   if (j < 12) {
@@ -75,22 +84,44 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_forward(StepArgs a, int change)
   s_a1[j] = h;
   s_a[j] = h;
   __syncthreads();
+  // hidden layers: each warp forms four outputs at a time, its lanes reading the four weight
+  // rows coalesced (lane l takes columns l, l + 32, l + 64, l + 96) and summing by shuffles
+  __shared__ float s_z[H];
+  const int lane = j & 31, warp = j >> 5;
   for (int l = 1; l <= 4; ++l) {
-    const float* W = th + mlp_w(l) + (size_t)j * H;
-    z = th[mlp_b(l) + j];
-    for (int k = 0; k < H; ++k) z = fmaf(W[k], s_a[k], z);
+    const float* W = th + mlp_w(l);
+    const float a0 = s_a[lane], a1 = s_a[lane + 32], a2 = s_a[lane + 64], a3 = s_a[lane + 96];
+    for (int o0 = warp * 4; o0 < H; o0 += 16) {
+      float acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float* Wr = W + (size_t)(o0 + u) * H;
+        acc[u] = fmaf(Wr[lane], a0, fmaf(Wr[lane + 32], a1, fmaf(Wr[lane + 64], a2, Wr[lane + 96] * a3)));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], off);
+      if (lane < 4) s_z[o0 + lane] = th[mlp_b(l) + o0 + lane] + (lane == 0 ? acc[0] : lane == 1 ? acc[1] : lane == 2 ? acc[2] : acc[3]);
+    }
+    __syncthreads();  // every output is formed; every thread has read the layer's input
+    z = s_z[j];
     zs[l * H + j] = z;
     h = fmaxf(z, 0.f);
     if (l == 2) h += s_a1[j];  // the skip connection after the third layer
-    __syncthreads();           // every thread has read the layer's input
     s_a[j] = h;
     __syncthreads();
   }
-  if (j < 12) {
-    const float* W = th + mlp_w(5) + (size_t)j * H;
-    float y = th[mlp_b(5) + j];
-    for (int k = 0; k < H; ++k) y = fmaf(W[k], s_a[k], y);
-    s_y[j] = y;
+  {  // output layer: warp w forms outputs w, w + 4, w + 8
+    const float* W = th + mlp_w(5);
+    const float a0 = s_a[lane], a1 = s_a[lane + 32], a2 = s_a[lane + 64], a3 = s_a[lane + 96];
+    for (int o = warp; o < 12; o += 4) {
+      const float* Wr = W + (size_t)o * H;
+      float acc = fmaf(Wr[lane], a0, fmaf(Wr[lane + 32], a1, fmaf(Wr[lane + 64], a2, Wr[lane + 96] * a3)));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) s_y[o] = th[mlp_b(5) + o] + acc;
+    }
   }
   __syncthreads();
   if (j != 0) return;
@@ -147,6 +178,7 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_backward(StepArgs a) {
   const int v = blockIdx.x, j = threadIdx.x;
   const int sc = a.views[v].scene;
   const float* th = a.mlp_theta + (size_t)sc * kMlpParams;
+  prefetch_weights(th);
   __shared__ float s_dy[12], s_dz[H];
   if (j == 0) {
     // G = (g_v, g_w) at T = P^s: dL/dt = g_v, and (for the tangent dR = [w]x R that phi
@@ -219,6 +251,7 @@ __global__ void __launch_bounds__(kMlpHid) k_mlp_backward(StepArgs a) {
   for (int l = 4; l >= 1; --l) {
     const float* W = th + mlp_w(l);
     da = 0.f;
+#pragma unroll 16
     for (int i = 0; i < H; ++i) da = fmaf(W[(size_t)i * H + j], s_dz[i], da);  // (W_l^T dz_l)_j
     if (l == 3) dskip = da;  // a_3 = relu(z_2) + a_1
     if (l == 1) da += dskip;
@@ -270,6 +303,7 @@ __global__ void __launch_bounds__(kMlpUpdThreads) k_mlp_update(StepArgs a) {
     const int i = bias ? 0 : (k - mlp_w(l)) % mlp_in(l);
     const int dz_off = l == 5 ? 5 * H + o : l * H + o;
     float grad = 0.f;
+#pragma unroll 8
     for (int v = a.scene_view_off[sc]; v < a.scene_view_off[sc + 1]; ++v) {
       const float d = a.mlp_dz[(size_t)v * kMlpDz + dz_off];
       float in = 1.f;
