@@ -435,15 +435,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        epo._binding.epo_set_poses(s.handle, T_host.numpy())
-        epo._binding.epo_step(s.handle, 1)
-        epo._binding.epo_get_poses(s.handle, T_out.numpy())
-        epo._binding.epo_last_loss(s.handle, loss_out.numpy())
+        # one public call per step: pinned poses in, the step, poses and loss out, one sync
+        epo._binding.epo_step_host(s.handle, T_host.numpy(), T_out.numpy(), loss_out.numpy())
         T_host.copy_(T_out)
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": world * evals * e2e_steps / e2e_dt, "unit": UNIT,
            "h2d_bytes_per_step": int(T_host.numel() * 8),
-           "d2h_bytes_per_step": int(T_out.numel() * 8 + loss_out.numel() * 8)}
+           "d2h_bytes_per_step": int(T_out.numel() * 8 + loss_out.numel() * 8 + 8)}  # + the status word
 
     # roofline of the dominant kernel (fused loss + gradient edge kernel): the four taps of
     # every evaluation, plus every record once per step (shared by its view's pairs)

@@ -40,7 +40,7 @@ EXPORTED = [
     "epo_distance_field", "epo_round_bf16", "epo_last_loss", "epo_kernel_time", "epo_fixup_stats", "epo_stage_times",
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
     "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph", "epo_get_refinement",
-    "epo_set_pose_mlp", "epo_get_pose_mlp", "epo_get_pose_mlp_moments",
+    "epo_set_pose_mlp", "epo_get_pose_mlp", "epo_get_pose_mlp_moments", "epo_step_host",
 ]
 
 
@@ -326,6 +326,11 @@ def epo_get_pose_mlp(scene, n_scenes: int, n_views: int):
     d = np.zeros((n_views, 3), np.float32)
     _call("epo_get_pose_mlp", scene, _ptr(p), _ptr(d))
     return p, d
+
+
+def epo_step_host(scene, T_in=None, T_out=None, loss=None):
+    """One host-driven step (arrays: contiguous float64, pinned for asynchronous copies)."""
+    _call("epo_step_host", scene, _ptr(T_in), _ptr(T_out), _ptr(loss))
 
 
 def epo_get_pose_mlp_moments(scene, n_scenes: int, n_views: int):

@@ -142,6 +142,8 @@ struct epo_scene {
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
+  double* d_io = nullptr;     // [poses (12 n_views) | loss (n_scenes) | flag (one word)]
+  double* h_io = nullptr;     // pinned staging of d_io for epo_step_host
   int64_t device_bytes = 0;
   // stage timing events (options.timing): before setup, after setup, after the edge
   // kernel, after the pose kernel
@@ -783,7 +785,12 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_K64, (size_t)6 * nv);
     ALLOC(S->d_pair_acc, (size_t)kAcc * np);
     ALLOC(S->d_grad, (size_t)6 * nv);
-    ALLOC(S->d_loss, n_scenes);
+    // the poses, the per-scene loss and the status flag in one block, so that a host-driven
+    // step (epo_step_host) reads them back with a single copy
+    ALLOC(S->d_io, (size_t)12 * nv + n_scenes + 1);
+    S->d_T = S->d_io;
+    S->d_loss = S->d_io + 12 * (size_t)nv;
+    S->d_flag = reinterpret_cast<int32_t*>(S->d_io + 12 * (size_t)nv + n_scenes);
     ALLOC(S->d_m, (size_t)6 * nv);
     ALLOC(S->d_v, (size_t)6 * nv);
     ALLOC(S->d_bpow, 2);
@@ -793,10 +800,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       ALLOC(S->d_tile_counter, 1);
     }
     ALLOC(S->d_lambda, 1);
-    ALLOC(S->d_T, (size_t)12 * nv);
     ALLOC(S->d_T_eval, (size_t)12 * nv);
     ALLOC(S->d_step, 1);
-    ALLOC(S->d_flag, 1);
     ALLOC(S->d_done, 1);
     std::vector<int32_t> chunk_off(1, 0), chunk_scene;
     for (int sc = 0; sc < n_scenes; ++sc) {
@@ -894,6 +899,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       for (const ViewDev& w : S->views) S->max_view_records = std::max(S->max_view_records, w.n_rec);
     }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
+    CK(cudaMallocHost(&S->h_io, ((size_t)12 * nv + n_scenes + 1) * 8));
     cudaStream_t st = S->stream;
     if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(S->d_map, 0, (size_t)S->map_elems * map_size, st));
@@ -1064,6 +1070,7 @@ void destroy_impl(epo_scene* S) {
   for (auto& b : S->bufs)
     if (b.p) cudaFree(b.p);
   if (S->h_flag) cudaFreeHost(S->h_flag);
+  if (S->h_io) cudaFreeHost(S->h_io);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
   delete S;
 }
@@ -1377,6 +1384,33 @@ epo_status epo_step_async(epo_scene_t S, int32_t n_steps) {
   st = ensure_graph(S);
   if (st != EPO_OK) return st;
   for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(S->graph, S->stream));
+  return EPO_OK;
+}
+
+epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, double* loss) {
+  if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
+  const size_t nv = (size_t)S->n_views;
+  if (T_in) {
+    if (S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "under the pose MLP the poses come from its parameters");
+    for (size_t k = 0; k < 12 * nv; ++k)
+      if (!isfinite(T_in[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
+    CK(cudaMemcpyAsync(S->d_T, T_in, 12 * nv * 8, cudaMemcpyHostToDevice, S->stream));
+  }
+  epo_status st = epo_step_async(S, 1);
+  if (st != EPO_OK) return st;
+  // poses, loss and flag in one copy (they are adjacent on the device)
+  const size_t io = 12 * nv + (size_t)S->n_scenes + 1;
+  CK(cudaMemcpyAsync(S->h_io, S->d_io, io * 8, cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (T_out) memcpy(T_out, S->h_io, 12 * nv * 8);
+  if (loss) memcpy(loss, S->h_io + 12 * nv, (size_t)S->n_scenes * 8);
+  int32_t flag;
+  memcpy(&flag, S->h_io + 12 * nv + S->n_scenes, 4);
+  if (flag & 1) {
+    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
+  }
   return EPO_OK;
 }
 

@@ -489,3 +489,24 @@ def test_gather_probe_rates_and_argument_checks():
         with pytest.raises(epo.EpoError) as e:
             B.epo_gather_probe(a["n_maps"], a["W"], a["H"], a["map_dtype"], a["gather"], a["pattern"], 1000, 1)
         assert e.value.status == B.EPO_ERR_INVALID_ARG
+
+
+def test_step_host_equals_separate_calls(ring8):
+    """epo_step_host (poses in, one step, poses and loss out, one synchronisation) gives what
+    epo_set_poses + epo_step + epo_get_poses + epo_last_loss give."""
+    B = epo._binding
+    sc, maps = ring8
+    a, b = gpu_scene(sc, maps), gpu_scene(sc, maps)
+    T = np.ascontiguousarray(np.asarray(sc.T_init, dtype=np.float64).reshape(-1, 12))
+    Ta, la = np.zeros_like(T), np.zeros(1)
+    B.epo_step_host(a.handle, T, Ta, la)
+    b.set_poses(T)
+    b.step(1)
+    lb = np.zeros(1)
+    B.epo_last_loss(b.handle, lb)
+    assert np.abs(Ta - b.get_poses().reshape(-1, 12)).max() < 1e-12
+    assert la[0] == pytest.approx(lb[0], rel=1e-12)
+    with pytest.raises(epo.EpoError):
+        bad = T.copy()
+        bad[0, 0] = np.nan
+        B.epo_step_host(a.handle, bad, None, None)
