@@ -100,7 +100,11 @@ struct AmbEntry {
   float u, v, z;
   int p;
 };
-constexpr int kAmbCap = 512;  // entries per block; re-evaluated once more than half full
+constexpr int kAmbCap = 512;  // entries per block
+// re-evaluated once more than kAmbRun are buffered: earlier than half full, so that less of the
+// work is left for the end of the kernel (measured: 1.3 % faster on the 200-view walk than at
+// 256, neutral on the 32-view ring; after every tile it is 8 % slower)
+constexpr int kAmbRun = 64;
 
 // The exact path.  The lift and the transform run in FP64; every decision (in front, in
 // bounds, bilinear cell, clamp) is then the one the FP64 evaluation of the definition takes,
@@ -466,9 +470,9 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     }
     if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
-    // exact path: when the buffer is more than half full, and once more before exiting
+    // exact path: when the buffer holds more than kAmbRun entries, and once more before exiting
     const int n_amb = min(s_amb_n, kAmbCap);
-    if (n_amb > (s_tile < a.n_tiles ? kAmbCap / 2 : 0)) {
+    if (n_amb > (s_tile < a.n_tiles ? kAmbRun : 0)) {
       for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, REC, MAP, REF>(a, s_amb[k], REF ? s_amb_rec[k] : (int64_t)0, lam64, lam);
       __syncthreads();
       if (threadIdx.x == 0) {
