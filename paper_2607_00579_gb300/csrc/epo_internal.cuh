@@ -48,8 +48,8 @@ __device__ __forceinline__ void load_record(const void* base, int64_t idx, float
   }
 }
 
-constexpr int kAcc = 8;
-constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)  // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
+constexpr int kAcc = 8;         // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
+constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)
 
 enum Mode { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2 };
 enum Gather { GATHER_LDG = 1, GATHER_TEX = 2 };
