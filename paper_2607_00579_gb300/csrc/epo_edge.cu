@@ -267,14 +267,14 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
         const float X0 = xt * z, X1 = yt * z;
         // rounding-error bound of Y = R X + t: 8u|X|_1 (rotation, lift, the rounded refined
         // focal length and depth, FMA roundings)
-        const float XA = idx < td.n ? 8.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
+        const float XA = idx < td.n ? 8.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -INFINITY;
         s_X[idx] = make_float4(X0, X1, z, XA);
         s_UV[idx] = make_float2(xt, yt);
       } else {
         const float X0 = (u - vi.cx) / vfx * z, X1 = (v - vi.cy) / vfy * z;
         // rounding-error bound of Y = R X + t: 6u|X|_1 (rotation, lift and FMA roundings);
-        // a record past the tile end gets w < 0 and is skipped
-        const float XA = idx < td.n ? 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -1.f;
+        // a record past the tile end gets w = -inf: never in front, never ambiguous
+        const float XA = idx < td.n ? 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)) : -INFINITY;
         s_X[idx] = make_float4(X0, X1, z, XA);
         s_UV[idx] = make_float2(u, v);
       }
@@ -298,24 +298,29 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 #pragma unroll
       for (int g = 0; g < RPT; g += ILP) {
         // phase A: project every sample and take the decisions the FP32 bound allows
-        float Y0[ILP], Y1[ILP], Y2[ILP], iz[ILP], up[ILP], vp[ILP], tu[ILP], tv[ILP];
+        // Y = R X + t enters below only through Y3 and the normalised coordinates
+        // (xn, yn) = (Y1, Y2) / Y3
+        float Y2[ILP], iz[ILP], xn[ILP], yn[ILP], up[ILP], vp[ILP], tu[ILP], tv[ILP];
         bool ok[ILP], amb[ILP];
         int x0[ILP], y0[ILP];
   #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
-          Y0[r] = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
-          Y1[r] = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
+          const float Y0 = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
+          const float Y1 = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
           Y2[r] = fmaf(P.r[6], X.x, fmaf(P.r[7], X.y, fmaf(P.r[8], X.z, P.t[2])));
-          const float E = X.w + P.Et;  // |Y_k - Y_k(exact)| <= E
-          const bool front = (X.w >= 0.f) && (Y2[r] > eps_z - E);
+          // |Y_k - Y_k(exact)| <= E; a record past the tile end has X.w = -inf, so that
+          // it is never in front and never ambiguous
+          const float E = X.w + P.Et;
+          const bool front = Y2[r] > eps_z - E;
           iz[r] = front ? rcp_approx(Y2[r]) : 0.f;
-          const float xn = Y0[r] * iz[r], yn = Y1[r] * iz[r];
-          up[r] = fmaf(P.fx, xn, P.cx);
-          vp[r] = fmaf(P.fy, yn, P.cy);
+          xn[r] = Y0 * iz[r];
+          yn[r] = Y1 * iz[r];
+          up[r] = fmaf(P.fx, xn[r], P.cx);
+          vp[r] = fmaf(P.fy, yn[r], P.cy);
           const float Eiz = E * iz[r];
-          tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn), Eiz), P.cu);  // bound on |u' - u'(exact)|
-          tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn), Eiz), P.cv);
+          tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn[r]), Eiz), P.cu);  // bound on |u' - u'(exact)|
+          tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn[r]), Eiz), P.cv);
           const bool cand = front && (fabsf(up[r] - P.hw) <= P.hw + tu[r]) && (fabsf(vp[r] - P.hh) <= P.hh + tv[r]);
           // within the bound of an integer coordinate (cell lines and the border are integers)
           // or of the depth threshold: the branch taken must come from the exact evaluation
@@ -393,27 +398,32 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
           }
           float dzs = 0.f;  // refine, fused pass: the sample's d(rho)/dz (0 unless valid)
           if (ok[r]) {
-            // a5: clamp + Huber
+            // a5: clamp + Huber.  With ch = min(|min(d, lambda)|, delta),
+            // H(min(d, lambda)) = ch (|min(d, lambda)| - ch / 2), both branches of Eq. 7 in one
+            // form; H'(d) = d clamped to [-delta, delta], passed where d <= lambda
             const float dh = fminf(d, lam);
-            const float adh = fabsf(dh);
-            const float rho = adh <= delta ? 0.5f * dh * dh : delta * (adh - 0.5f * delta);
+            const float ch = fminf(fabsf(dh), delta);
+            const float rho = ch * fmaf(-0.5f, ch, fabsf(dh));
             if constexpr (MODE != MODE_BWD) {
               acc[0] += rho;
               acc[1] += 1.f;
             }
             if constexpr (MODE != MODE_FWD) {
-              // a6: adjoint in camera-j coordinates
-              const float drho = d <= lam ? (fabsf(d) <= delta ? d : copysignf(delta, d)) : 0.f;
-              const float gx = drho * ddu * P.fx * iz[r];
-              const float gy = drho * ddv * P.fy * iz[r];
-              const float gz = -(gx * Y0[r] + gy * Y1[r]) * iz[r];
-              acc[2] += gx;
-              acc[3] += gy;
-              acc[4] += gz;
-              acc[5] += Y1[r] * gz - Y2[r] * gy;
-              acc[6] += Y2[r] * gx - Y0[r] * gz;
-              acc[7] += Y0[r] * gy - Y1[r] * gx;
+              // a6: adjoint in camera-j coordinates.  With (ga, gb) = H' (fx dd/du', fy dd/dv')
+              // and gc = -(ga xn + gb yn), the gradient at Y is g = (ga, gb, gc) / Y3 and, as
+              // Y = Y3 (xn, yn, 1), Y x g = (xn, yn, 1) x (ga, gb, gc): no 1/Y3 factor there
+              const float drho = d <= lam ? fmaxf(fminf(d, delta), -delta) : 0.f;
+              const float ga = drho * (P.fx * ddu);
+              const float gb = drho * (P.fy * ddv);
+              const float gc = -fmaf(ga, xn[r], gb * yn[r]);
+              acc[2] = fmaf(ga, iz[r], acc[2]);
+              acc[3] = fmaf(gb, iz[r], acc[3]);
+              acc[4] = fmaf(gc, iz[r], acc[4]);
+              acc[5] += fmaf(yn[r], gc, -gb);
+              acc[6] += fmaf(-xn[r], gc, ga);
+              acc[7] += fmaf(xn[r], gb, -(yn[r] * ga));
               if constexpr (REF) {
+                const float gx = ga * iz[r], gy = gb * iz[r], gz = gc * iz[r];
                 // dY/dz = R (x~, y~, 1): dRho/dz = g . dY/dz; the source focal term
                 // -g . R (X0, X1, 0) = z (g . r_2 - dRho/dz) (times 1 + gamma_i) and the
                 // target focal term gx Y0 + gy Y1 (times 1 + gamma_j)
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
                                  gz * fmaf(P.r[6], xy.x, fmaf(P.r[7], xy.y, P.r[8]));
                 const float gr2 = gx * P.r[2] + gy * P.r[5] + gz * P.r[8];
                 facc0 += zr * (gr2 - dz);
-                facc1 += gx * Y0[r] + gy * Y1[r];
+                facc1 -= gc;  // gx Y0 + gy Y1 = ga xn + gb yn
                 dzs = dz;
               }
             }
