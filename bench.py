@@ -432,10 +432,14 @@ def run_ours(args):
     T_out = torch.empty_like(T_host).pin_memory()
     loss_out = torch.empty(info.n_scenes, dtype=torch.float64).pin_memory()
     e2e_steps = max(10, args.steps // 2)
+    # untimed warm-up: the first call captures the host-step graph
+    for _ in range(3):
+        epo._binding.epo_step_host(s.handle, T_host.numpy(), T_out.numpy(), loss_out.numpy())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        # one public call per step: pinned poses in, the step, poses and loss out, one sync
+        # one public call per step: poses in, the step, poses and loss out, one sync (the
+        # step's graph reads and writes the scene's mapped pinned staging)
         epo._binding.epo_step_host(s.handle, T_host.numpy(), T_out.numpy(), loss_out.numpy())
         T_host.copy_(T_out)
     e2e_dt = time.perf_counter() - t0

@@ -251,9 +251,11 @@ epo_status epo_step_async(epo_scene_t scene, int32_t n_steps);
  * T_in (n_views x 12 doubles, host; NULL keeps the current ones; not allowed under
  * EPO_POSE_MLP, whose poses come from its parameters) are copied in, the step runs, and the
  * poses after it (T_out, n_views x 12) and the loss it evaluated (loss, n_scenes) are copied
- * out; either output may be NULL.  With pinned host buffers the copies are asynchronous on
- * the scene's stream.  EPO_ERR_INVALID_ARG on a non-finite input pose, EPO_ERR_NUMERIC as
- * epo_step. */
+ * out; either output may be NULL.  The caller's buffers may be any host memory: the scene
+ * keeps a pinned, device-mapped staging buffer, which the step's graph reads the poses from
+ * (its first kernel) and writes poses, loss and status back into (its last kernel), so no
+ * copy-engine transfer sits between the host and the step.  EPO_ERR_INVALID_ARG on a
+ * non-finite input pose, EPO_ERR_NUMERIC as epo_step. */
 epo_status epo_step_host(epo_scene_t scene, const double* T_in, double* T_out, double* loss);
 /* The per-step form without the graph: the same kernels launched one by
  * one from the host every step (the plain form the graph is compared to). */

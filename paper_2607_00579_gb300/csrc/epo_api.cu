@@ -143,14 +143,20 @@ struct epo_scene {
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
   double* d_io = nullptr;     // [poses (12 n_views) | loss (n_scenes) | flag (one word)]
-  double* h_io = nullptr;     // pinned staging of d_io for epo_step_host
+  // epo_step_host's staging, pinned and mapped: h_in = [flag | poses (12 n_views)], h_io a copy
+  // of d_io; dh_in, dh_io are their device addresses, read and written by the step's graph
+  double* h_in = nullptr;
+  double* h_io = nullptr;
+  const double* dh_in = nullptr;
+  double* dh_io = nullptr;
   int64_t device_bytes = 0;
   // stage timing events (options.timing): before setup, after setup, after the edge
   // kernel, after the pose kernel
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
-  // graph of one optimisation step
+  // graph of one optimisation step, and the same step between the copies of epo_step_host
   cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_host = nullptr;
   bool graph_dirty = true;
   std::string err;
 };
@@ -544,17 +550,20 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   return EPO_OK;
 }
 
-epo_status ensure_graph(epo_scene* S) {
-  // build the tile table outside capture (it allocates)
-  epo_status st = build_tiles(S);
+// The host-driven step (epo_step_host): the poses from the mapped staging (if its flag is set),
+// the step, then poses, loss and flag to the mapped staging, all in one graph.
+epo_status enqueue_host_step(epo_scene* S, cudaStream_t s) {
+  const int64_t nv = S->n_views;
+  CK(launch_io_copy(S->dh_in + 1, S->d_T, 12 * nv, S->dh_in, s));
+  epo_status st = enqueue_step(S, s);
   if (st != EPO_OK) return st;
-  if (!S->graph_dirty && S->graph) return EPO_OK;
-  if (S->graph) {
-    cudaGraphExecDestroy(S->graph);
-    S->graph = nullptr;
-  }
+  CK(launch_io_copy(S->d_io, S->dh_io, 12 * nv + S->n_scenes + 1, nullptr, s));
+  return EPO_OK;
+}
+
+epo_status capture(epo_scene* S, bool host, cudaGraphExec_t* out) {
   CK(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
-  st = enqueue_step(S, S->cap_stream);
+  epo_status st = host ? enqueue_host_step(S, S->cap_stream) : enqueue_step(S, S->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
   if (st != EPO_OK) {
@@ -562,10 +571,27 @@ epo_status ensure_graph(epo_scene* S) {
     return st;
   }
   if (e != cudaSuccess) return cuda_fail(S, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&S->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(S, e, "cudaGraphInstantiate");
-  S->graph_dirty = false;
+  return EPO_OK;
+}
+
+// (Re)captures the step graph when the schedule or the tile table changed; the host-step
+// graph is dropped with it and captured again on its next use.
+epo_status ensure_graph(epo_scene* S, bool host = false) {
+  // build the tile table outside capture (it allocates)
+  epo_status st = build_tiles(S);
+  if (st != EPO_OK) return st;
+  if (S->graph_dirty || !S->graph) {
+    if (S->graph) cudaGraphExecDestroy(S->graph);
+    if (S->graph_host) cudaGraphExecDestroy(S->graph_host);
+    S->graph = S->graph_host = nullptr;
+    st = capture(S, false, &S->graph);
+    if (st != EPO_OK) return st;
+    S->graph_dirty = false;
+  }
+  if (host && !S->graph_host) return capture(S, true, &S->graph_host);
   return EPO_OK;
 }
 
@@ -899,7 +925,16 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       for (const ViewDev& w : S->views) S->max_view_records = std::max(S->max_view_records, w.n_rec);
     }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
-    CK(cudaMallocHost(&S->h_io, ((size_t)12 * nv + n_scenes + 1) * 8));
+    CK(cudaHostAlloc(&S->h_io, ((size_t)12 * nv + n_scenes + 1) * 8, cudaHostAllocMapped));
+    CK(cudaHostAlloc(&S->h_in, ((size_t)12 * nv + 1) * 8, cudaHostAllocMapped));
+    S->h_in[0] = 0.0;
+    {
+      void* d = nullptr;
+      CK(cudaHostGetDevicePointer(&d, S->h_io, 0));
+      S->dh_io = reinterpret_cast<double*>(d);
+      CK(cudaHostGetDevicePointer(&d, S->h_in, 0));
+      S->dh_in = reinterpret_cast<const double*>(d);
+    }
     cudaStream_t st = S->stream;
     if (!rec_host.empty()) CK(cudaMemcpyAsync(S->d_rec, rec_host.data(), rec_host.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(S->d_map, 0, (size_t)S->map_elems * map_size, st));
@@ -1061,6 +1096,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
 void destroy_impl(epo_scene* S) {
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
+  if (S->graph_host) cudaGraphExecDestroy(S->graph_host);
   for (auto e2 : S->ev)
     if (e2) cudaEventDestroy(e2);
   for (auto t : S->tex)
@@ -1071,6 +1107,7 @@ void destroy_impl(epo_scene* S) {
     if (b.p) cudaFree(b.p);
   if (S->h_flag) cudaFreeHost(S->h_flag);
   if (S->h_io) cudaFreeHost(S->h_io);
+  if (S->h_in) cudaFreeHost(S->h_in);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
   delete S;
 }
@@ -1394,13 +1431,16 @@ epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, doubl
     if (S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "under the pose MLP the poses come from its parameters");
     for (size_t k = 0; k < 12 * nv; ++k)
       if (!isfinite(T_in[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
-    CK(cudaMemcpyAsync(S->d_T, T_in, 12 * nv * 8, cudaMemcpyHostToDevice, S->stream));
   }
-  epo_status st = epo_step_async(S, 1);
+  epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
-  // poses, loss and flag in one copy (they are adjacent on the device)
-  const size_t io = 12 * nv + (size_t)S->n_scenes + 1;
-  CK(cudaMemcpyAsync(S->h_io, S->d_io, io * 8, cudaMemcpyDeviceToHost, S->stream));
+  st = ensure_graph(S, true);
+  if (st != EPO_OK) return st;
+  // the staging is pinned and mapped: the graph's first kernel reads the poses from it and its
+  // last kernel writes poses, loss and flag (adjacent on the device) back into it
+  if (T_in) memcpy(S->h_in + 1, T_in, 12 * nv * 8);
+  S->h_in[0] = T_in ? 1.0 : 0.0;
+  CK(cudaGraphLaunch(S->graph_host, S->stream));
   CK(cudaStreamSynchronize(S->stream));
   if (T_out) memcpy(T_out, S->h_io, 12 * nv * 8);
   if (loss) memcpy(loss, S->h_io + 12 * nv, (size_t)S->n_scenes * 8);

@@ -829,6 +829,26 @@ cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Copy of n doubles between device memory and mapped pinned host memory, inside a step's
+// graph (the host-driven step): the GPU reads and writes the host buffer directly, so no copy
+// engine round trip sits on the step's critical path.  With `flag`, the copy happens only if
+// *flag != 0; the flag and the data are loaded together, so the host latency is paid once.
+// Host memory is read with ld.global.cv (no stale line from an earlier step).
+__global__ void __launch_bounds__(256) k_io_copy(const double* src, double* dst, int64_t n, const double* flag) {
+  const double f = flag ? __ldcv(flag) : 1.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double x = __ldcv(src + k);
+    if (f != 0.0) dst[k] = x;
+  }
+}
+
+cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, const double* flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 64);
+  k_io_copy<<<grid, 256, 0, s>>>(src, dst, n, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_twist_poses(const double* T, const double* xi, double* T_out, int n,
                                cudaStream_t s) {
   k_twist_poses<<<(n + 127) / 128, 128, 0, s>>>(T, xi, T_out, n);

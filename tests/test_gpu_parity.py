@@ -506,6 +506,20 @@ def test_step_host_equals_separate_calls(ring8):
     B.epo_last_loss(b.handle, lb)
     assert np.abs(Ta - b.get_poses().reshape(-1, 12)).max() < 1e-12
     assert la[0] == pytest.approx(lb[0], rel=1e-12)
+    # consecutive calls through the same staging: poses fed back, then a call that keeps the
+    # device's poses (T_in NULL), then one after steps queued without synchronisation
+    for _ in range(3):
+        B.epo_step_host(a.handle, Ta.copy(), Ta, la)
+        b.step(1)
+    B.epo_step_host(a.handle, None, Ta, la)
+    b.step(1)
+    B.epo_step_async(a.handle, 2)
+    b.step(2)
+    B.epo_step_host(a.handle, None, Ta, la)
+    b.step(1)
+    B.epo_last_loss(b.handle, lb)
+    assert np.abs(Ta - b.get_poses().reshape(-1, 12)).max() < 1e-12
+    assert la[0] == pytest.approx(lb[0], rel=1e-12)
     with pytest.raises(epo.EpoError):
         bad = T.copy()
         bad[0, 0] = np.nan
