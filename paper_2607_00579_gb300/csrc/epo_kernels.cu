@@ -136,6 +136,19 @@ __device__ constexpr double kExpA[5] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 504
 __device__ constexpr double kExpB[5] = {0.5, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0};
 __device__ constexpr double kExpC[5] = {1.0 / 6.0, -1.0 / 120.0, 1.0 / 5040.0, -1.0 / 362880.0, 1.0 / 39916800.0};
 
+// R = I, t = 0: the relative pose a target entry of the pose gather reads
+__device__ __align__(16) const double kIdentityPose[12] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+
+// 1/n for a sample count n >= 1: the FP32 approximate reciprocal (relative error below
+// 2^-22 after rounding n to FP32) refined by one FP64 Newton step, relative error below 2^-43:
+// two FP64 operations instead of a correctly rounded FP64 reciprocal
+__device__ __forceinline__ double rcp_count(double n) {
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)n));
+  const double r = (double)rf;
+  return fma(r, fma(-n, r, 1.0), r);
+}
+
 // Entry (r, c) of [w]x = [[0, -w2, w1], [w2, 0, -w0], [-w1, w0, 0]] with runtime r, c.
 __device__ __forceinline__ double cross_entry(int r, int c, double w0, double w1, double w2) {
   if (r == c) return 0.0;
@@ -178,50 +191,73 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     }
     // a scene whose schedule has converged keeps its poses
     const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
-    double g[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    double gg = 0.0;  // refine scenes: dL/dgamma_v, before the 1 / (1 + gamma_v) factor
+    // the lane's partial sums: dL/dxi_v (six components), then (refine scenes) dL/dgamma_v
+    // before its 1 / (1 + gamma_v) factor, then a zero pad
+    double g[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (vv) {
       const PoseEntry* ent = a.pose_entries + (size_t)v * a.pose_stride;
       for (int k = e; k < a.pose_stride; k += 16) {
         const PoseEntry en = ent[k];
         if (en.p < 0) continue;
         const int p = en.p;
-        const double* acc = a.pair_acc + (size_t)kAcc * p;
+        const bool src = (en.scene_role & 1) != 0;
+        // the pair's sums (frame j), weight and relative pose are loaded together; a target
+        // entry reads T_ji = I, so that both roles run the same instructions
+        const double2* acc = reinterpret_cast<const double2*>(a.pair_acc + (size_t)kAcc * p);
+        const double2* Rt = reinterpret_cast<const double2*>(src ? a.pp64 + 12 * (size_t)p : kIdentityPose);
+        const double2 s01 = acc[0], s23 = acc[1], s45 = acc[2], s67 = acc[3];
+        const double2 R01 = Rt[0], R23 = Rt[1], R45 = Rt[2], R67 = Rt[3], R8t0 = Rt[4], t12 = Rt[5];
         double c = a.pair_lw[p];  // the pair's weight in its scene's loss (0: not evaluated)
         if (c == 0.0) continue;
         if (!a.norm_all) {
-          const double n = acc[1];  // Algorithm 3: the pair's mean runs over its valid samples
+          const double n = s01.y;  // Algorithm 3: the pair's mean runs over its valid samples
           if (!(n > 0.0)) continue;
-          c *= __drcp_rn(n);
+          c *= rcp_count(n);
         }
         if (a.gscale) c *= a.gscale[en.scene_role >> 1];
-        const double ga0 = c * acc[2], ga1 = c * acc[3], ga2 = c * acc[4];
-        const double gb0 = c * acc[5], gb1 = c * acc[6], gb2 = c * acc[7];
-        if (a.refine) gg += c * a.pair_facc[2 * (size_t)p + ((en.scene_role & 1) ? 0 : 1)];
-        if ((en.scene_role & 1) == 0) {  // target view j: the 6-vector as is
-          g[0] += ga0; g[1] += ga1; g[2] += ga2;
-          g[3] += gb0; g[4] += gb1; g[5] += gb2;
-        } else {
-          // source view i: -Ad(T_ji)^T (ga, gb) = (-R^T ga, R^T (t x ga) - R^T gb)
-          const double* R = a.pp64 + 12 * (size_t)p;
-          const double x0 = R[10] * ga2 - R[11] * ga1 - gb0;
-          const double x1 = R[11] * ga0 - R[9] * ga2 - gb1;
-          const double x2 = R[9] * ga1 - R[10] * ga0 - gb2;
+        if (a.refine) g[6] += c * a.pair_facc[2 * (size_t)p + (src ? 0 : 1)];
+        // the entry adds s (R^T ga, R^T (gb - t x ga)), (ga, gb) = c (sum g_Y, sum Y x g_Y):
+        // the target's 6-vector as is (s = 1, R = I, t = 0) and the source's
+        // -Ad(T_ji)^T (ga, gb) = (-R^T ga, R^T (t x ga) - R^T gb) (s = -1)
+        if (src) c = -c;
+        const double R[9] = {R01.x, R01.y, R23.x, R23.y, R45.x, R45.y, R67.x, R67.y, R8t0.x};
+        const double t0 = R8t0.y, t1 = t12.x, t2 = t12.y;
+        const double ga0 = c * s23.x, ga1 = c * s23.y, ga2 = c * s45.x;
+        const double gb0 = c * s45.y, gb1 = c * s67.x, gb2 = c * s67.y;
+        const double x0 = fma(t2, ga1, fma(-t1, ga2, gb0));
+        const double x1 = fma(t0, ga2, fma(-t2, ga0, gb1));
+        const double x2 = fma(t1, ga0, fma(-t0, ga1, gb2));
 #pragma unroll
-          for (int k3 = 0; k3 < 3; ++k3) {
-            g[k3] -= R[k3] * ga0 + R[3 + k3] * ga1 + R[6 + k3] * ga2;
-            g[3 + k3] += R[k3] * x0 + R[3 + k3] * x1 + R[6 + k3] * x2;
-          }
+        for (int k3 = 0; k3 < 3; ++k3) {
+          g[k3] = fma(R[6 + k3], ga2, fma(R[3 + k3], ga1, fma(R[k3], ga0, g[k3])));
+          g[3 + k3] = fma(R[6 + k3], x2, fma(R[3 + k3], x1, fma(R[k3], x0, g[3 + k3])));
         }
       }
     }
-    // fixed-order reduction over the 16 lanes of the pose
+    // fixed-order reduce-scatter over the pose's 16 lanes (8 FP64 additions instead of 4 per
+    // value): lane e = 8 b3 + 4 b2 + 2 b1 + b0 ends with the sum of value 4 b3 + 2 b2 + b1, so
+    // value k sits in lanes 2k and 2k + 1
+    double sred;
+    {
+      const bool b3 = e & 8, b2 = e & 4, b1 = e & 2;
+      double k4[4], k2[2];
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) {
+      for (int i = 0; i < 4; ++i) {
+        const double keep = b3 ? g[4 + i] : g[i], send = b3 ? g[i] : g[4 + i];
+        k4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
-      if (a.refine) gg += __shfl_xor_sync(0xffffffffu, gg, o);
+      for (int i = 0; i < 2; ++i) {
+        const double keep = b2 ? k4[2 + i] : k4[i], send = b2 ? k4[i] : k4[2 + i];
+        k2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      const double keep = b1 ? k2[1] : k2[0], send = b1 ? k2[0] : k2[1];
+      sred = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+      sred += __shfl_xor_sync(0xffffffffu, sred, 1);
     }
+    // lane e < 6 takes component e of the gradient
+    const double G = __shfl_sync(0xffffffffu, sred, base + 2 * (e < 6 ? e : 0));
+    const double gg = __shfl_sync(0xffffffffu, sred, base + 12);
     if (a.refine && vv && e == 0) {
       const double g0 = a.gamma[v];
       const double Gg = gg / (1.0 + g0);  // dL/dgamma_v
@@ -240,10 +276,6 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         }
       }
     }
-    double G = 0.0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (e == k) G = g[k];
     if (vv && e < 6) {
       a.grad[6 * (size_t)v + e] = G;
       if (!isfinite(G)) atomicOr(a.flag, 1);
@@ -275,13 +307,20 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       const int r = (e >> 2) < 3 ? (e >> 2) : 2, c = e & 3;
       const double w0 = x[3], w1 = x[4], w2 = x[5];
       const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-      double A, B, C;
-      if (th2 < 2.5e-3) {
-        // theta < 0.05: Taylor polynomials in theta^2, truncation below 1e-20
-        A = fma(th2, fma(th2, fma(th2, fma(th2, kExpA[4], kExpA[3]), kExpA[2]), kExpA[1]), kExpA[0]);
-        B = fma(th2, fma(th2, fma(th2, fma(th2, kExpB[4], kExpB[3]), kExpB[2]), kExpB[1]), kExpB[0]);
-        C = fma(th2, fma(th2, fma(th2, fma(th2, kExpC[4], kExpC[3]), kExpC[2]), kExpC[1]), kExpC[0]);
-      } else {
+      // theta < 0.05: Taylor polynomials in theta^2, truncation below 1e-20; lanes 0, 1, 2 of
+      // the pose evaluate A, B, C (one polynomial per lane) and share them
+      double tay;
+      {
+        const int q = e % 3;
+        double co[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) co[i] = q == 0 ? kExpA[i] : (q == 1 ? kExpB[i] : kExpC[i]);
+        tay = fma(th2, fma(th2, fma(th2, fma(th2, co[4], co[3]), co[2]), co[1]), co[0]);
+      }
+      double A = __shfl_sync(0xffffffffu, tay, base);
+      double B = __shfl_sync(0xffffffffu, tay, base + 1);
+      double C = __shfl_sync(0xffffffffu, tay, base + 2);
+      if (!(th2 < 2.5e-3)) {
         const double th = sqrt(th2);
         double sn, cs;
         sincos(th, &sn, &cs);
@@ -296,14 +335,17 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         const double I = r == c ? 1.0 : 0.0;
         Erc = I + A * cross_entry(r, c, w0, w1, w2) + B * (wr * wc - I * th2);
       } else {
-        // translation: (I + B W + C W^2) upsilon, row r
-        Erc = 0.0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const double wk = k == 0 ? w0 : (k == 1 ? w1 : w2);
-          const double I = r == k ? 1.0 : 0.0;
-          Erc = fma(I + B * cross_entry(r, k, w0, w1, w2) + C * (wr * wk - I * th2), x[k], Erc);
-        }
+        // translation: (I + B W + C W^2) upsilon = upsilon + B (w x upsilon) + C (w x (w x upsilon)),
+        // row r
+        const double p0 = fma(w1, x[2], -w2 * x[1]);
+        const double p1 = fma(w2, x[0], -w0 * x[2]);
+        const double p2 = fma(w0, x[1], -w1 * x[0]);
+        const double pr = r == 0 ? p0 : (r == 1 ? p1 : p2);
+        const double wa = r == 0 ? w1 : (r == 1 ? w2 : w0), wb = r == 0 ? w2 : (r == 1 ? w0 : w1);
+        const double pa = r == 0 ? p1 : (r == 1 ? p2 : p0), pb = r == 0 ? p2 : (r == 1 ? p0 : p1);
+        const double qr = fma(wa, pb, -wb * pa);  // (w x p)_r
+        const double ur = r == 0 ? x[0] : (r == 1 ? x[1] : x[2]);
+        Erc = fma(C, qr, fma(B, pr, ur));
       }
       const int rb = base + (e & 12);
       const double E0 = __shfl_sync(0xffffffffu, Erc, rb);
