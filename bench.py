@@ -476,7 +476,8 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MB write, then 256 MB read back)",
                        "schedule": {"gather": info.gather, "block": info.block_threads,
                                     "records_per_thread": info.records_per_thread,
-                                    "grid": info.grid_blocks},
+                                    "grid": info.grid_blocks, "tail_pairs": info.tail_pairs,
+                                    "work_items": info.n_tiles},
                        "parallelism": f"replicas x{world}" if world > 1 else "single"},
             "gpu_launches": info.kernels_per_step * args.steps, "clocks": clk, "e2e": e2e, "roofline": roof,
             "gather_roofline": gather_roof,

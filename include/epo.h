@@ -116,7 +116,8 @@ typedef struct {
                                 0 = each covers all of its view's pairs, like the others;
                                 n > 0 = split into items of at most n pairs, so that the
                                 blocks finish together; -1 = default (autotuned when
-                                autotune is on, else 0) */
+                                autotune is on, else 0); n <= -2 = every work item, not
+                                only the last wave's, covers at most -n pairs */
   int32_t refine;            /* 1: the scene also carries the focal and depth refinement of
                                 Section 3 (Eq. 4: f_i = f_i^0 (1 + gamma_i) for both focal
                                 lengths of view i; Eq. 5: every edge pixel's depth is
@@ -167,7 +168,8 @@ typedef struct {
   int32_t n_tiles;           /* work items of the persistent kernels */
   int32_t gather, block_threads, records_per_thread, grid_blocks; /* schedule in use */
   int32_t kernels_per_step;  /* kernel launches in one epo_step */
-  int32_t tail_pairs;        /* pairs per work item of the last wave (0 = not split) */
+  int32_t tail_pairs;        /* pairs per work item of the last wave (0 = not split; a
+                                negative n: every work item covers at most -n pairs) */
 } epo_scene_info;
 
 /* Defaults: delta 1, lambda 10 -> 6 over 1000 steps, eps_z 1e-6, NORM_VALID,

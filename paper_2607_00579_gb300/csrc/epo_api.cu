@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <string>
 #include <vector>
 
@@ -409,9 +410,11 @@ epo_status build_tiles(epo_scene* S, int tile, int tail, int grid) {
   return EPO_OK;
 }
 
-// Work items of a schedule: block * rpt records each; the last wave is one item per
-// resident block.
+// Work items of a schedule: block * rpt records each; with tail > 0 the last wave is one item
+// per resident block (items of at most `tail` pairs), with tail < 0 every item covers at most
+// -tail pairs (more, smaller items).
 epo_status build_tiles(epo_scene* S, int gather, int rpt, int block, int tail) {
+  if (tail < 0) return build_tiles(S, block * rpt, -tail, INT_MAX);
   return build_tiles(S, block * rpt, tail, tail ? resident_blocks(S, gather, rpt, block) : 0);
 }
 
@@ -617,7 +620,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 1, 2 or 4");
   if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
-  if (o.tail_pairs < -1) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs must be -1, 0 or positive");
+  if (o.tail_pairs == INT_MIN) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs out of range");
   if (o.refine != 0 && o.refine != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "refine must be 0 or 1");
   if (o.pair_budget < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "pair_budget must be >= 0");
   if (o.schedule != 0 && o.schedule != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "schedule must be 0 or 1");
@@ -1084,7 +1087,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     S->rpt = o.records_per_thread ? o.records_per_thread : 2;
     S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG;
     if (!schedule_fits(S, S->rpt, S->block)) S->block = 128;
-    S->tail = o.tail_pairs > 0 ? o.tail_pairs : 0;
+    S->tail = o.tail_pairs == -1 ? 0 : o.tail_pairs;
     epo_status bs = build_tiles(S);
     if (bs != EPO_OK) return bs;
     CK(cudaStreamSynchronize(st));
@@ -1632,7 +1635,8 @@ epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
 // thermal drift during tuning affects all of them alike, and each candidate is judged by
 // the median of its launches. A first pass over all candidates (3 timed launches each)
 // keeps the 4 best; with tail_pairs = -1 each of those is also tried with its last wave
-// split into items of 2 pairs and of 1 pair, and 12 further passes decide.
+// split into items of 2 pairs and of 1 pair, and 12 further passes decide.  (Every item split
+// by pairs, tail_pairs <= -2, was never faster on the benchmark workloads: not a candidate.)
 epo_status epo_autotune(epo_scene_t S) {
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   S->tuned = true;  // also guards against recursion through maybe_autotune
@@ -1641,7 +1645,7 @@ epo_status epo_autotune(epo_scene_t S) {
     std::vector<float> ms;
     float med;
   };
-  const int tail0 = S->opt.tail_pairs > 0 ? S->opt.tail_pairs : 0;
+  const int tail0 = S->opt.tail_pairs == -1 ? 0 : S->opt.tail_pairs;
   std::vector<Cand> cands;
   for (int g : {GATHER_LDG, GATHER_TEX})
     for (int r : {1, 2, 4})

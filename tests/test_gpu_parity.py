@@ -146,6 +146,30 @@ def test_split_last_wave_matches_oracle(ring8, tail):
     assert loss[0] == pytest.approx(l0[0], rel=1e-12) and grad_rel_err(grad, g0) < 1e-10
 
 
+@pytest.mark.parametrize("split", [2, 3])
+def test_split_every_item_matches_oracle(ring8, split):
+    """Every work item split into items of at most `split` pairs (tail_pairs = -split), on a
+    grid of two blocks, so that the items run in many waves."""
+    sc, maps = ring8
+    s = gpu_scene(sc, maps, tail_pairs=-split, grid_blocks=2)
+    assert s.info().tail_pairs == -split
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=s.pair_stats())
+    last = gpu_scene(sc, maps, tail_pairs=split, grid_blocks=2)
+    ref = gpu_scene(sc, maps, tail_pairs=0, grid_blocks=2)
+    ks = set(np.bincount(np.asarray(sc.pairs)[:, 0]).tolist())  # all ordered pairs: k per view
+    assert len(ks) == 1
+    k = ks.pop()
+    assert s.info().n_tiles == ref.info().n_tiles * -(-k // split)
+    assert s.info().n_tiles > last.info().n_tiles > ref.info().n_tiles
+    for h in (last, ref):
+        h.set_poses(sc.T_init)
+        l0, g0 = h.loss_and_grad()
+        assert loss[0] == pytest.approx(l0[0], rel=1e-12) and grad_rel_err(grad, g0) < 1e-10
+
+
 def test_gather_paths_and_schedules_agree(ring8):
     sc, maps = ring8
     res = []
