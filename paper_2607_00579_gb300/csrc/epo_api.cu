@@ -104,7 +104,7 @@ struct epo_scene {
   int max_pairs = 1;
   int64_t* d_step = nullptr;
   int32_t* d_flag = nullptr;
-  unsigned int* d_done = nullptr;
+  unsigned long long* d_done = nullptr;
   // loss chunks: 32 consecutive pairs of one scene per pose-kernel block
   int32_t n_loss_chunks = 0;
   int32_t *d_loss_chunk_off = nullptr, *d_loss_chunk_scene = nullptr;
@@ -994,7 +994,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     CK(cudaMemsetAsync(S->d_qoverflow, 0, 4, st));
     CK(cudaMemsetAsync(S->d_step, 0, 8, st));
     CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
-    CK(cudaMemsetAsync(S->d_done, 0, 4, st));
+    CK(cudaMemsetAsync(S->d_done, 0, 8, st));
     CK(cudaMemsetAsync(S->d_scene_done, 0, 4 * (size_t)n_scenes, st));
     CK(cudaMemcpyAsync(S->d_loss_chunk_off, chunk_off.data(), chunk_off.size() * 4, cudaMemcpyHostToDevice, st));
     if (!chunk_pairs.empty())

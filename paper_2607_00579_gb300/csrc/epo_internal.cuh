@@ -168,7 +168,7 @@ struct StepArgs {
   int64_t* step;
   double* lambda;
   int32_t* flag;                     // bit 0: non-finite loss/gradient
-  unsigned int* done;                // completion counter of the pose kernel
+  unsigned long long* done;          // completion counter of the pose kernel (blocks | flagged << 32)
   int32_t n_loss_chunks;             // pose-kernel blocks that sum the per-pair losses
   const int32_t* loss_chunk_off;     // n_scenes + 1: the scene's chunks (kLossChunk pairs each)
   const int32_t* loss_chunk_scene;   // n_loss_chunks

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
   static_assert(kPoseThreads == 32 && kLossChunk == 32, "one warp per block, one pair per lane");
   const int64_t step = *a.step;
   const int flag0 = *a.flag;
+  bool bad_here = false;  // this thread set the non-finite flag in this step
   if ((int)blockIdx.x < n_pose_blocks) {
     const int lane = threadIdx.x & 31;
     const int base = lane & 16;
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         // factors are the pose optimiser's (the same step count)
         if (!isfinite(Gg)) {
           atomicOr(a.flag, 1);
+          bad_here = true;
         } else if (!(flag0 & 1) && !conv) {
           const double m = a.beta1 * mg_old + (1.0 - a.beta1) * Gg;
           const double vm = a.beta2 * vg_old + (1.0 - a.beta2) * Gg * Gg;
@@ -278,7 +280,10 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     }
     if (vv && e < 6) {
       a.grad[6 * (size_t)v + e] = G;
-      if (!isfinite(G)) atomicOr(a.flag, 1);
+      if (!isfinite(G)) {
+        atomicOr(a.flag, 1);
+        bad_here = true;
+      }
     }
     if (with_grad == 2) {
       const bool bad = vv && e < 6 && !isfinite(G);
@@ -424,28 +429,31 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       if (threadIdx.x == 0) {
         const double L = t;  // the weights carry the 2 / (active pairs) factor
         a.loss[s] = L;
-        if (!isfinite(L)) atomicOr(a.flag, 1);
+        if (!isfinite(L)) {
+          atomicOr(a.flag, 1);
+          bad_here = true;
+        }
         a.scene_done[s] = 0u;
       }
     }
   }
   if (with_grad == 2 && !a.pose_mlp) {
     // the last block to finish advances the step counter and the beta powers (under the pose
-    // MLP its update kernel does)
-    __syncwarp();
+    // MLP its update kernel does), unless the step began flagged or a block flagged it.  The
+    // blocks report completion and their flag in one atomic: low word a count, high word the
+    // flagged blocks, so that no fence is needed (the last block reads nothing else that the
+    // others wrote in this kernel)
+    const bool bad_block = __any_sync(0xffffffffu, bad_here);
     if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned int prev = atomicAdd(a.done, 1u);
-      if (prev == gridDim.x - 1) {
-        __threadfence();
-        const int flag_now = atomicOr(a.flag, 0);
-        if (!(flag_now & 1)) {
+      const unsigned long long add = 1ull + (bad_block ? (1ull << 32) : 0ull);
+      const unsigned long long prev = atomicAdd(a.done, add);
+      if ((unsigned int)prev == gridDim.x - 1) {
+        if (!(flag0 & 1) && ((prev + add) >> 32) == 0ull) {
           *a.step = step + 1;
           a.bpow[0] *= a.beta1;
           a.bpow[1] *= a.beta2;
         }
-        *a.done = 0u;
-        __threadfence();
+        *a.done = 0ull;
       }
     }
   }
