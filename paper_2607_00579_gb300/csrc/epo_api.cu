@@ -144,8 +144,8 @@ struct epo_scene {
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
   double* d_io = nullptr;     // [poses (12 n_views) | loss (n_scenes) | flag (one word)]
-  // epo_step_host's staging, pinned and mapped: h_in = [flag | poses (12 n_views)], h_io a copy
-  // of d_io; dh_in, dh_io are their device addresses, read and written by the step's graph
+  // epo_step_host's staging, pinned and mapped: h_in the input poses (12 n_views), h_io the
+  // layout of d_io; dh_in, dh_io are their device addresses, read and written by the step's graph
   double* h_in = nullptr;
   double* h_io = nullptr;
   const double* dh_in = nullptr;
@@ -155,9 +155,10 @@ struct epo_scene {
   // kernel, after the pose kernel
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
-  // graph of one optimisation step, and the same step between the copies of epo_step_host
+  // graph of one optimisation step, and the host-driven steps of epo_step_host without and
+  // with input poses
   cudaGraphExec_t graph = nullptr;
-  cudaGraphExec_t graph_host = nullptr;
+  cudaGraphExec_t graph_host[2] = {nullptr, nullptr};
   bool graph_dirty = true;
   std::string err;
 };
@@ -532,8 +533,11 @@ epo_status enqueue_loss_grad(epo_scene* S, cudaStream_t s, const double* T_eval)
 // Refine scenes: the fused pass also stores every sample's d(rho)/dz; the pose kernel updates
 // the poses and gamma, and with the depth module (lr_depth > 0) the depth kernel weights those
 // derivatives by the pairs' w / n and updates alpha and beta.
-epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
+// host_out: the mapped output block of the host-driven step, written by the pose kernel
+// (NULL: none)
+epo_status enqueue_step(epo_scene* S, cudaStream_t s, double* host_out = nullptr) {
   StepArgs a = step_args(S, S->d_T, nullptr);
+  a.host_out = host_out;
   MARK(0, s);
   if (S->subsample) CK(launch_subsample(a, s));
   if (S->refine) CK(launch_refine_intrinsics(a, s));
@@ -553,20 +557,24 @@ epo_status enqueue_step(epo_scene* S, cudaStream_t s) {
   return EPO_OK;
 }
 
-// The host-driven step (epo_step_host): the poses from the mapped staging (if its flag is set),
-// the step, then poses, loss and flag to the mapped staging, all in one graph.
-epo_status enqueue_host_step(epo_scene* S, cudaStream_t s) {
-  const int64_t nv = S->n_views;
-  CK(launch_io_copy(S->dh_in + 1, S->d_T, 12 * nv, S->dh_in, s));
-  epo_status st = enqueue_step(S, s);
+// The host-driven step (epo_step_host) in one graph: a copy kernel brings the input poses from
+// the mapped staging (with_in; timed against the pair setup reading them itself, which was
+// slower: its uncached host reads cost more than the launch), and the pose kernel writes
+// poses, loss and status word into the mapped output block when it is the step's last
+// kernel; otherwise a copy kernel does.
+epo_status enqueue_host_step(epo_scene* S, cudaStream_t s, bool with_in) {
+  const bool fold_out = !S->pose_mlp && !S->depth_opt && !S->opt.schedule;
+  if (with_in) CK(launch_io_copy(S->dh_in, S->d_T, 12 * (int64_t)S->n_views, s));
+  epo_status st = enqueue_step(S, s, fold_out ? S->dh_io : nullptr);
   if (st != EPO_OK) return st;
-  CK(launch_io_copy(S->d_io, S->dh_io, 12 * nv + S->n_scenes + 1, nullptr, s));
+  if (!fold_out) CK(launch_io_copy(S->d_io, S->dh_io, 12 * (int64_t)S->n_views + S->n_scenes + 1, s));
   return EPO_OK;
 }
 
-epo_status capture(epo_scene* S, bool host, cudaGraphExec_t* out) {
+// host: 0 the plain step, 1 the host-driven step keeping the device's poses, 2 with input poses
+epo_status capture(epo_scene* S, int host, cudaGraphExec_t* out) {
   CK(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
-  epo_status st = host ? enqueue_host_step(S, S->cap_stream) : enqueue_step(S, S->cap_stream);
+  epo_status st = host ? enqueue_host_step(S, S->cap_stream, host == 2) : enqueue_step(S, S->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(S->cap_stream, &g);
   if (st != EPO_OK) {
@@ -581,20 +589,21 @@ epo_status capture(epo_scene* S, bool host, cudaGraphExec_t* out) {
 }
 
 // (Re)captures the step graph when the schedule or the tile table changed; the host-step
-// graph is dropped with it and captured again on its next use.
-epo_status ensure_graph(epo_scene* S, bool host = false) {
+// graphs are dropped with it and captured again on their next use.  host: as in capture().
+epo_status ensure_graph(epo_scene* S, int host = 0) {
   // build the tile table outside capture (it allocates)
   epo_status st = build_tiles(S);
   if (st != EPO_OK) return st;
   if (S->graph_dirty || !S->graph) {
     if (S->graph) cudaGraphExecDestroy(S->graph);
-    if (S->graph_host) cudaGraphExecDestroy(S->graph_host);
-    S->graph = S->graph_host = nullptr;
-    st = capture(S, false, &S->graph);
+    for (auto& g : S->graph_host)
+      if (g) cudaGraphExecDestroy(g);
+    S->graph = S->graph_host[0] = S->graph_host[1] = nullptr;
+    st = capture(S, 0, &S->graph);
     if (st != EPO_OK) return st;
     S->graph_dirty = false;
   }
-  if (host && !S->graph_host) return capture(S, true, &S->graph_host);
+  if (host && !S->graph_host[host - 1]) return capture(S, host, &S->graph_host[host - 1]);
   return EPO_OK;
 }
 
@@ -929,8 +938,9 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
     CK(cudaHostAlloc(&S->h_io, ((size_t)12 * nv + n_scenes + 1) * 8, cudaHostAllocMapped));
-    CK(cudaHostAlloc(&S->h_in, ((size_t)12 * nv + 1) * 8, cudaHostAllocMapped));
-    S->h_in[0] = 0.0;
+    CK(cudaHostAlloc(&S->h_in, (size_t)12 * nv * 8, cudaHostAllocMapped));
+    memset(S->h_io, 0, ((size_t)12 * nv + n_scenes + 1) * 8);
+    memset(S->h_in, 0, (size_t)12 * nv * 8);
     {
       void* d = nullptr;
       CK(cudaHostGetDevicePointer(&d, S->h_io, 0));
@@ -1099,7 +1109,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
 void destroy_impl(epo_scene* S) {
   if (!S) return;
   if (S->graph) cudaGraphExecDestroy(S->graph);
-  if (S->graph_host) cudaGraphExecDestroy(S->graph_host);
+  for (auto g : S->graph_host)
+    if (g) cudaGraphExecDestroy(g);
   for (auto e2 : S->ev)
     if (e2) cudaEventDestroy(e2);
   for (auto t : S->tex)
@@ -1437,13 +1448,14 @@ epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, doubl
   }
   epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
-  st = ensure_graph(S, true);
+  const int which = T_in ? 2 : 1;
+  st = ensure_graph(S, which);
   if (st != EPO_OK) return st;
-  // the staging is pinned and mapped: the graph's first kernel reads the poses from it and its
-  // last kernel writes poses, loss and flag (adjacent on the device) back into it
-  if (T_in) memcpy(S->h_in + 1, T_in, 12 * nv * 8);
-  S->h_in[0] = T_in ? 1.0 : 0.0;
-  CK(cudaGraphLaunch(S->graph_host, S->stream));
+  // the staging is pinned and mapped: the step's pair setup reads the poses from it, and its
+  // pose kernel (or a copy kernel after the step's last kernel) writes poses, loss and status
+  // word back into it
+  if (T_in) memcpy(S->h_in, T_in, 12 * nv * 8);
+  CK(cudaGraphLaunch(S->graph_host[which - 1], S->stream));
   CK(cudaStreamSynchronize(S->stream));
   if (T_out) memcpy(T_out, S->h_io, 12 * nv * 8);
   if (loss) memcpy(loss, S->h_io + 12 * nv, (size_t)S->n_scenes * 8);

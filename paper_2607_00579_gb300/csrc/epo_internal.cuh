@@ -157,6 +157,9 @@ struct StepArgs {
   const uint8_t* fixed;
   const double* T;                   // poses used by the evaluation (n_views x 12)
   double* T_store;                   // poses updated by the retraction
+  // host-driven step (epo_step_host): mapped host memory (NULL if unused) that receives the
+  // poses after the step, the loss and the status word from the pose kernel
+  double* host_out;
   PairParam* pp;
   double* pp64;
   double* pair_acc;
@@ -267,7 +270,7 @@ cudaError_t launch_edge(const EdgeArgs& a, int mode, int refine, int rec_dtype, 
                         int rpt, int block, int grid, cudaStream_t s);
 // pose kernel: with_grad 0 = loss only, 1 = loss + gradient, 2 = + Adam/Exp update
 cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s);
-cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, const double* flag, cudaStream_t s);
+cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t launch_twist_poses(const double* T, const double* xi, double* T_out, int n,
                                cudaStream_t s);
 cudaError_t launch_apply_left_jacobian(const double* xi, const double* g, double* out, int n,

@@ -361,6 +361,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       if (!skip && e < 12) Tnew = fma(E0, Tc0, fma(E1, Tc1, fma(E2, Tc2, c == 3 ? E3 : 0.0)));
       __syncwarp();  // every lane has read the old pose before any lane writes it
       if (!skip && e < 12) a.T_store[12 * (size_t)v + e] = Tnew;
+      if (a.host_out && vv && e < 12)  // host-driven step: every pose, updated or kept
+        a.host_out[12 * (size_t)v + e] = skip ? (r == 0 ? Tc0 : (r == 1 ? Tc1 : Tc2)) : Tnew;
       if (a.schedule && !a.pose_mlp) {
         // the step's pose change (Section 3, Optimization Schedule): lane (r, c) holds entry
         // (r, c) of the old and the new pose; tr(R_new R_old^T) and the translations' dot
@@ -429,6 +431,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       if (threadIdx.x == 0) {
         const double L = t;  // the weights carry the 2 / (active pairs) factor
         a.loss[s] = L;
+        if (a.host_out) a.host_out[12 * (size_t)a.n_views + s] = L;
         if (!isfinite(L)) {
           atomicOr(a.flag, 1);
           bad_here = true;
@@ -453,6 +456,9 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
           a.bpow[0] *= a.beta1;
           a.bpow[1] *= a.beta2;
         }
+        if (a.host_out)  // the step's status word: the flag it began with or set
+          *reinterpret_cast<int32_t*>(a.host_out + 12 * (size_t)a.n_views + a.n_scenes) =
+              flag0 | (((prev + add) >> 32) ? 1 : 0);
         *a.done = 0ull;
       }
     }
@@ -881,21 +887,17 @@ cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s) {
 
 // Copy of n doubles between device memory and mapped pinned host memory, inside a step's
 // graph (the host-driven step): the GPU reads and writes the host buffer directly, so no copy
-// engine round trip sits on the step's critical path.  With `flag`, the copy happens only if
-// *flag != 0; the flag and the data are loaded together, so the host latency is paid once.
-// Host memory is read with ld.global.cv (no stale line from an earlier step).
-__global__ void __launch_bounds__(256) k_io_copy(const double* src, double* dst, int64_t n, const double* flag) {
-  const double f = flag ? __ldcv(flag) : 1.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const double x = __ldcv(src + k);
-    if (f != 0.0) dst[k] = x;
-  }
+// engine round trip sits on the step's critical path.  Reads use ld.global.cv, so that a line
+// of host memory cached by an earlier step is fetched again.
+__global__ void __launch_bounds__(256) k_io_copy(const double* src, double* dst, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = __ldcv(src + k);
 }
 
-cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, const double* flag, cudaStream_t s) {
+cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 64);
-  k_io_copy<<<grid, 256, 0, s>>>(src, dst, n, flag);
+  k_io_copy<<<grid, 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 

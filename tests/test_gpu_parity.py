@@ -515,12 +515,16 @@ def test_gather_probe_rates_and_argument_checks():
         assert e.value.status == B.EPO_ERR_INVALID_ARG
 
 
-def test_step_host_equals_separate_calls(ring8):
+@pytest.mark.parametrize("opts", [{}, {"schedule": 1}, {"refine": 1, "lr_focal": 1e-3, "lr_depth": 1e-3}],
+                         ids=["pose-kernel-last", "schedule-last", "depth-kernel-last"])
+def test_step_host_equals_separate_calls(ring8, opts):
     """epo_step_host (poses in, one step, poses and loss out, one synchronisation) gives what
-    epo_set_poses + epo_step + epo_get_poses + epo_last_loss give."""
+    epo_set_poses + epo_step + epo_get_poses + epo_last_loss give: with the pose kernel as the
+    step's last kernel (it writes the host outputs itself) and with a later kernel (a copy
+    kernel writes them)."""
     B = epo._binding
     sc, maps = ring8
-    a, b = gpu_scene(sc, maps), gpu_scene(sc, maps)
+    a, b = gpu_scene(sc, maps, **opts), gpu_scene(sc, maps, **opts)
     T = np.ascontiguousarray(np.asarray(sc.T_init, dtype=np.float64).reshape(-1, 12))
     Ta, la = np.zeros_like(T), np.zeros(1)
     B.epo_step_host(a.handle, T, Ta, la)
