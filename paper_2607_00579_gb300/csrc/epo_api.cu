@@ -96,6 +96,7 @@ struct epo_scene {
   std::vector<cudaTextureObject_t> tex;
   std::vector<cudaArray_t> arrays;
   PairParam* d_pp = nullptr;
+  int32_t* d_pair_q = nullptr;  // the PairParam index of every pair (source-view order)
   double *d_pp64 = nullptr, *d_K64 = nullptr, *d_pair_acc = nullptr, *d_grad = nullptr,
          *d_loss = nullptr, *d_m = nullptr, *d_v = nullptr, *d_bpow = nullptr, *d_lambda = nullptr,
          *d_T = nullptr, *d_T_eval = nullptr;
@@ -253,6 +254,7 @@ StepArgs step_args(epo_scene* S, const double* T_eval, const double* gscale) {
   a.T = T_eval;
   a.T_store = S->d_T;
   a.pp = S->d_pp;
+  a.pair_q = S->d_pair_q;
   a.pp64 = S->d_pp64;
   a.pair_acc = S->d_pair_acc;
   a.grad = S->d_grad;
@@ -819,6 +821,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_fixed, nv);
     ALLOC(S->d_tex, nv);
     ALLOC(S->d_pp, np);
+    ALLOC(S->d_pair_q, np);
     ALLOC(S->d_pp64, (size_t)12 * np);
     ALLOC(S->d_K64, (size_t)6 * nv);
     ALLOC(S->d_pair_acc, (size_t)kAcc * np);
@@ -1060,13 +1063,15 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     // the relative pose and its bound each step)
     {
       std::vector<PairParam> pp(np);
+      std::vector<int32_t> pair_q(np);
+      for (int k = 0; k < np; ++k) pair_q[S->src_pair_ids[k]] = k;
       for (int p = 0; p < np; ++p) {
-        PairParam& q = pp[p];
+        PairParam& q = pp[pair_q[p]];
         memset(&q, 0, sizeof(q));
         const ViewDev& vj = S->views[S->pair_dst[p]];
         q.fx = vj.fx; q.fy = vj.fy; q.cx = vj.cx; q.cy = vj.cy;
-        q.fx2 = 2.f * vj.fx;
-        q.fy2 = 2.f * vj.fy;
+        q.p = p;
+        q.active = 1;  // the pair setup copies the step's flag
         q.hw = 0.5f * (float)(vj.W - 1);
         q.hh = 0.5f * (float)(vj.H - 1);
         q.cu = 4.f * kU32 * (float)(vj.W + 1);
@@ -1079,11 +1084,12 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
         int64_t run = 0;
         for (int v = 0; v < nv; ++v)
           for (int k = S->src_pair_off[v]; k < S->src_pair_off[v + 1]; ++k) {
-            pp[S->src_pair_ids[k]].dbase = run - S->views[v].rec_begin;
+            pp[k].dbase = run - S->views[v].rec_begin;
             run += S->views[v].n_rec;
           }
       }
       CK(cudaMemcpyAsync(S->d_pp, pp.data(), (size_t)np * sizeof(PairParam), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(S->d_pair_q, pair_q.data(), (size_t)np * 4, cudaMemcpyHostToDevice, st));
       CK(cudaStreamSynchronize(st));
     }
     {

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kDepthThreads) k_depth(StepArgs a, int chunks_
       if (act) {  // the weight w_p / n_p from the pose kernel's loss blocks
         const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
         s_w[pos] = a.pair_wz[p];
-        s_base[pos] = a.pp[p].dbase;
+        s_base[pos] = a.pp[q0 + k].dbase;
       }
       cnt += __popc(bal);
     }

@@ -98,7 +98,8 @@ __device__ __forceinline__ int scatter_slot(int lane) {
 // pair, kept in shared memory until the block re-evaluates it with FP64 decisions.
 struct AmbEntry {
   float u, v, z;
-  int p;
+  int p;  // the pair
+  int q;  // its PairParam
 };
 constexpr int kAmbCap = 512;  // entries per block
 // re-evaluated once more than kAmbRun are buffered: earlier than half full, so that less of the
@@ -122,7 +123,7 @@ template <int MODE, int REC, int MAP, int REF>
 __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, double lam, float lamf) {
   const int p = en.p;
   const int i = a.pair_src[p];
-  const PairParam& P = a.pp[p];
+  const PairParam& P = a.pp[en.q];
   // K64 holds fx, fy, cx, cy followed by 1/fx, 1/fy (refine scenes: at f0 (1 + gamma))
   const double* Ki = a.K64 + 6 * (size_t)i;
   const double* Kj = a.K64 + 6 * (size_t)a.pair_dst[p];
@@ -239,14 +240,14 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   const float eps_z = a.eps_z;
   const double lam64 = *a.lambda;
   if (threadIdx.x == 0) {
-    s_tile = atomicAdd(a.tile_counter, 1);
+    s_tile = blockIdx.x;  // the first work item is the block's own; later ones are claimed
     s_amb_n = 0;
   }
   __syncthreads();
   while (s_tile < a.n_tiles) {
     const int t = s_tile;
     // claim the next tile now: the atomic's round trip overlaps this tile's work
-    if (threadIdx.x == 0) s_next = atomicAdd(a.tile_counter, 1);
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(a.tile_counter, 1);
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
     float vfx = vi.fx, vfy = vi.fy;
@@ -284,9 +285,12 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     const int pb = __ldg(&a.tiles[t].q0);
     const int pe = __ldg(&a.tiles[t].q1);
     for (int q = pb; q < pe; ++q) {
-      const int p = a.src_pair_ids[q];
-      if (!a.pair_active[p]) continue;  // uniform over the block
-      const PairParam P = a.pp[p];
+      // the pair's index and flag first (one 8-byte load), the rest once it is evaluated:
+      // holding every field from before the branch costs registers
+      const int2 pact = *reinterpret_cast<const int2*>(&a.pp[q].p);
+      if (!pact.y) continue;  // uniform over the block
+      const int p = pact.x;
+      const PairParam P = a.pp[q];
       const float Wm1 = (float)(P.W - 1), Hm1 = (float)(P.H - 1);
       float acc[8];
 #pragma unroll
@@ -318,9 +322,9 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
           yn[r] = Y1 * iz[r];
           up[r] = fmaf(P.fx, xn[r], P.cx);
           vp[r] = fmaf(P.fy, yn[r], P.cy);
-          const float Eiz = E * iz[r];
-          tu[r] = fmaf(P.fx2, fmaf(Eiz, fabsf(xn[r]), Eiz), P.cu);  // bound on |u' - u'(exact)|
-          tv[r] = fmaf(P.fy2, fmaf(Eiz, fabsf(yn[r]), Eiz), P.cv);
+          const float Eiz = 2.f * E * iz[r];  // with the bound's 2x safety factor
+          tu[r] = fmaf(P.fx, fmaf(Eiz, fabsf(xn[r]), Eiz), P.cu);  // bound on |u' - u'(exact)|
+          tv[r] = fmaf(P.fy, fmaf(Eiz, fabsf(yn[r]), Eiz), P.cv);
           const bool cand = front && (fabsf(up[r] - P.hw) <= P.hw + tu[r]) && (fabsf(vp[r] - P.hh) <= P.hh + tv[r]);
           // within the bound of an integer coordinate (cell lines and the border are integers)
           // or of the depth threshold: the branch taken must come from the exact evaluation
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
               if (pos < kAmbCap) {
                 const int li = threadIdx.x + (g + r) * blockDim.x;
                 const float2 uv = s_UV[li];  // refine scenes: reloaded from the record
-                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p};
+                s_amb[pos] = AmbEntry{uv.x, uv.y, s_X[li].z, p, q};
                 if constexpr (REF) s_amb_rec[pos] = td.begin + li;
               } else {
                 // buffer full: evaluate this sample with FP32 decisions instead
@@ -469,8 +473,9 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     const int nq = (pe - pb) * NS;
     for (int k = threadIdx.x; k < nq; k += blockDim.x) {
       const int qq = k / NS, slot = S0 + k % NS;
-      const int p = a.src_pair_ids[pb + qq];
-      if (!a.pair_active[p]) continue;
+      const int2 pact = *reinterpret_cast<const int2*>(&a.pp[pb + qq].p);
+      if (!pact.y) continue;
+      const int p = pact.x;
       float s = 0.f;
       for (int w = 0; w < nwarp; ++w) s += s_part[((size_t)w * a.max_pairs + qq) * NSLOT + slot];
       if (s != 0.f) {

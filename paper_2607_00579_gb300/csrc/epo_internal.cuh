@@ -23,6 +23,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace epo {
@@ -74,15 +75,18 @@ struct TileDev {
 
 // Everything the edge kernel needs for one pair i -> j, built by the pair setup (a1):
 // the relative pose T_ji = T_j T_i^-1 rounded to f32, the target's intrinsics and map,
-// and the pair constants of the FP32 rounding-error bound.  128 bytes, read with eight
-// uniform 16-byte loads per pair.
+// the pair constants of the FP32 rounding-error bound, and the pair's index and flag.  128
+// bytes, read with eight uniform 16-byte loads per pair.  Stored in the order of the views'
+// outgoing pair lists (entry q of src_pair_ids), so that a work item reads its pairs' entries
+// directly, with no pair-list or flag load in front of them.
 struct alignas(16) PairParam {
   float r[9];
   float t[3];
   float fx, fy, cx, cy;   // target intrinsics (f32)
   float hw, hh;           // (W-1)/2, (H-1)/2: the valid range is |u' - hw| <= hw
+  int32_t p;              // the pair's index (p and active are read as one 8-byte word)
+  int32_t active;         // the pair is evaluated in this step (copied from pair_active)
   float Et;               // rounding bound of Y from the rounded translation
-  float fx2, fy2;         // 2 fx, 2 fy (bound scale with a 2x safety factor)
   float cu, cv;           // rounding of u', v' themselves
   int32_t W, H, pitch;    // target map
   int64_t map_off;
@@ -90,6 +94,9 @@ struct alignas(16) PairParam {
   int64_t dbase;          // refine scenes: dzr[dbase + r] holds d(rho)/dz of record r for this pair
 };
 static_assert(sizeof(PairParam) == 128, "PairParam layout");
+static_assert(offsetof(PairParam, p) % 8 == 0 && offsetof(PairParam, active) == offsetof(PairParam, p) + 4,
+              "p and active form one aligned 8-byte word");
+static_assert(offsetof(PairParam, map_off) % 8 == 0 && offsetof(PairParam, dbase) % 8 == 0, "PairParam alignment");
 
 struct EdgeArgs {
   const void* rec;
@@ -102,7 +109,7 @@ struct EdgeArgs {
   const int32_t* src_pair_ids;   // pairs grouped by source view
   const int32_t* pair_src;       // n_pairs
   const int32_t* pair_dst;       // n_pairs
-  const PairParam* pp;           // n_pairs
+  const PairParam* pp;           // n_pairs, in source-view pair-list order (index q)
   const double* pp64;            // n_pairs x 12: R_ji (9), t_ji (3) in f64
   const uint8_t* pair_active;    // n_pairs
   const unsigned long long* tex; // n_views texture objects (GATHER_TEX)
@@ -160,7 +167,8 @@ struct StepArgs {
   // host-driven step (epo_step_host): mapped host memory (NULL if unused) that receives the
   // poses after the step, the loss and the status word from the pose kernel
   double* host_out;
-  PairParam* pp;
+  PairParam* pp;                     // n_pairs, in source-view pair-list order
+  const int32_t* pair_q;             // n_pairs: the PairParam index q of pair p
   double* pp64;
   double* pair_acc;
   double* grad;                      // n_views x 6

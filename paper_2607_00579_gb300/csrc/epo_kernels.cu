@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   const int p = gt / kSetupLanes;
   const bool pv = p < a.n_pairs;
   const int2 ij = pv ? a.pair_ij[p] : make_int2(0, 0);
+  const int q = pv ? a.pair_q[p] : 0;
+  const int act = pv && e == 13 ? (int)a.pair_active[p] : 0;
   const int i = ij.x, j = ij.y;
   const double* Ti = a.T + 12 * (size_t)i;
   const double* Tj = a.T + 12 * (size_t)j;
@@ -78,13 +80,15 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
     if (bad) atomicOr(a.flag, 1);  // a non-finite pose: the step must not update
   }
   if (!pv) return;
-  PairParam* out = a.pp + p;
+  PairParam* out = a.pp + q;
   float* of = reinterpret_cast<float*>(out);
   if (e < 12) {
     a.pp64[12 * (size_t)p + e] = val;  // R (9) then t (3), as in PairParam
     of[e] = vf;
   } else if (e == 15) {
     out->Et = 4.f * kU32 * (fabsf(t0) + fabsf(t1) + fabsf(t2));
+  } else if (e == 13) {
+    out->active = act;
   } else if (a.refine && e == 12) {
     // refine scenes: the target's intrinsics at f0 (1 + gamma_j) (Eq. 4), rounded to FP32;
     // the projection bound grows by one rounding of the focal length
@@ -92,8 +96,6 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
     const float fx = (float)(a.K64[6 * (size_t)j] * sc), fy = (float)(a.K64[6 * (size_t)j + 1] * sc);
     out->fx = fx;
     out->fy = fy;
-    out->fx2 = 2.f * fx;
-    out->fy2 = 2.f * fy;
     out->cu = 5.f * kU32 * (float)(out->W + 1);
     out->cv = 5.f * kU32 * (float)(out->H + 1);
   }
