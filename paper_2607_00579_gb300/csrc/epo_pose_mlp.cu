@@ -324,20 +324,19 @@ __global__ void __launch_bounds__(kMlpUpdThreads) k_mlp_update(StepArgs a) {
                                  a.mlp_wd_delta, a.mlp_eps);
   }
   // the last block to finish advances the step counter and the beta powers (read by the
-  // focal Adam of refine scenes)
+  // focal Adam of refine scenes).  The decision rests on the flag every block read at its
+  // start, and every block has used its step count before it reports, so the count needs no
+  // fence
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
     const unsigned int prev = atomicAdd(a.mlp_done, 1u);
     if (prev == gridDim.x - 1) {
-      __threadfence();
       if (!refused) {
         *a.step = step + 1;
         a.bpow[0] *= a.beta1;
         a.bpow[1] *= a.beta2;
       }
       *a.mlp_done = 0u;
-      __threadfence();
     }
   }
 }

@@ -182,6 +182,24 @@ def test_gather_paths_and_schedules_agree(ring8):
         assert grad_rel_err(g, res[0][1]) < 1e-6
 
 
+@pytest.mark.parametrize("grid", [1, 5000])
+def test_grid_sizes_agree(ring8, grid):
+    """A one-block grid (the block starts on item 0 and claims every later item in turn) and a
+    grid option far larger than the work list (capped at one block per item: every block runs
+    only its own first item) give the default grid's loss and gradient."""
+    sc, maps = ring8
+    ref = gpu_scene(sc, maps)
+    s = gpu_scene(sc, maps, grid_blocks=grid)
+    assert grid > s.info().n_tiles or grid == 1
+    for h in (ref, s):
+        h.set_poses(sc.T_init)
+    l0, g0 = ref.loss_and_grad()
+    l1, g1 = s.loss_and_grad()
+    assert l1[0] == pytest.approx(l0[0], rel=1e-12) and grad_rel_err(g1, g0) < 1e-10
+    o = oracle_of(sc, maps).loss_grad(sc.T_init, lam=10.0)
+    check_against_oracle(l1[0], g1, o, sc.pairs, sc.T_init, stats=s.pair_stats())
+
+
 def test_norm_all_mode(ring8):
     sc, maps = ring8
     s = gpu_scene(sc, maps, norm_mode=epo.EPO_NORM_ALL)
