@@ -235,10 +235,11 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   const int warp = threadIdx.x >> 5;
   const int nwarp = blockDim.x >> 5;
   const unsigned lanemask_lt = (1u << lane) - 1u;
-  const float lam = (float)(*a.lambda);
+  float lam = 0.f;     // the step's clamp, read once the pair setup has run
+  double lam64 = 0.0;
+  bool waited = false;
   const float delta = a.delta;
   const float eps_z = a.eps_z;
-  const double lam64 = *a.lambda;
   if (threadIdx.x == 0) {
     s_tile = blockIdx.x;  // the first work item is the block's own; later ones are claimed
     s_amb_n = 0;
@@ -246,8 +247,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   __syncthreads();
   while (s_tile < a.n_tiles) {
     const int t = s_tile;
-    // claim the next tile now: the atomic's round trip overlaps this tile's work
-    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(a.tile_counter, 1);
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
     float vfx = vi.fx, vfy = vi.fy;
@@ -280,6 +279,18 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
         s_UV[idx] = make_float2(u, v);
       }
     }
+    if (!waited) {
+      // everything from here on reads what the step's pair setup writes (PairParams, the clamp,
+      // the work counter, the zeroed pair sums): wait for it after the first item's records are
+      // lifted, so that this block's start overlaps the setup, then let the pose kernel start
+      griddep_wait();
+      griddep_launch_dependents();
+      lam64 = *a.lambda;
+      lam = (float)lam64;
+      waited = true;
+    }
+    // claim the next tile now: the atomic's round trip overlaps this tile's work
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(a.tile_counter, 1);
     // the item's pair range, loaded where it is needed (holding the whole item in
     // registers across the pair loop costs a block per SM)
     const int pb = __ldg(&a.tiles[t].q0);
@@ -513,8 +524,7 @@ static cudaError_t launch_edge_one(const EdgeArgs& a, int block, int grid, cudaS
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_edge<MODE, REC, MAP, GATHER, R, REF><<<grid, block, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_edge<MODE, REC, MAP, GATHER, R, REF>, dim3(grid), dim3(block), smem, s, a);
 }
 
 // Refine scenes run two records per thread only (one set of instantiations).

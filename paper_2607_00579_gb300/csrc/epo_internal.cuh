@@ -49,6 +49,13 @@ __device__ __forceinline__ void load_record(const void* base, int64_t idx, float
   }
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl() may start while its
+// predecessor in the stream still runs; griddep_wait() returns once that predecessor has
+// completed and its writes are visible (at once for a kernel launched without it), and
+// griddep_launch_dependents() lets the successor start early.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 constexpr int kAcc = 8;         // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
 constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)
 
@@ -278,6 +285,23 @@ cudaError_t launch_edge(const EdgeArgs& a, int mode, int refine, int rec_dtype, 
                         int rpt, int block, int grid, cudaStream_t s);
 // pose kernel: with_grad 0 = loss only, 1 = loss + gradient, 2 = + Adam/Exp update
 cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s);
+// A launch that allows programmatic dependent launch on stream s (see griddep_wait).
+template <typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t launch_twist_poses(const double* T, const double* xi, double* T_out, int n,
                                cudaStream_t s);

@@ -42,6 +42,7 @@ constexpr int kSetupLanes = 16;
 constexpr int kSetupThreads = 32;  // two pairs per block: the FP64 chains spread over SMs
 
 __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mode) {
+  griddep_launch_dependents();  // the edge kernel may start its first records meanwhile
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   if (gt == 0) {
     *a.lambda = lambda_at(a, *a.step);
@@ -194,6 +195,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     }
     // a scene whose schedule has converged keeps its poses
     const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
+    // the state loads above do not depend on the edge kernel; the pair sums below do
+    griddep_wait();
     // the lane's partial sums: dL/dxi_v (six components), then (refine scenes) dL/dgamma_v
     // before its 1 / (1 + gamma_v) factor, then a zero pad
     double g[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -395,6 +398,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     // per-scene loss (Eq. 6): this block sums l_p over kLossChunk consecutive pairs of one
     // scene (one pair per lane, fixed shuffle tree); the scene's last chunk to finish adds
     // the scene's partial sums in a fixed order, so the loss does not depend on timing
+    griddep_wait();  // the pair sums come from the edge kernel
     const int c = blockIdx.x - n_pose_blocks;
     const int s = a.loss_chunk_scene[c];
     const int2 range = a.loss_chunk_pairs[c];
@@ -883,8 +887,7 @@ cudaError_t launch_l2_read(const void* p, int64_t bytes, unsigned* sink, int sms
 
 cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s) {
   const int nbp = (a.n_views + kPosesPerBlock - 1) / kPosesPerBlock;
-  k_poses<<<nbp + a.n_loss_chunks, kPoseThreads, 0, s>>>(a, with_grad, nbp);
-  return cudaGetLastError();
+  return launch_pdl(k_poses, dim3(nbp + a.n_loss_chunks), dim3(kPoseThreads), 0, s, a, with_grad, nbp);
 }
 
 // Copy of n doubles between device memory and mapped pinned host memory, inside a step's
