@@ -822,7 +822,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     ALLOC(S->d_tex, nv);
     ALLOC(S->d_pp, np);
     ALLOC(S->d_pair_q, np);
-    ALLOC(S->d_pp64, (size_t)12 * np);
+    ALLOC(S->d_pp64, (size_t)kPP64 * np);
     ALLOC(S->d_K64, (size_t)6 * nv);
     ALLOC(S->d_pair_acc, (size_t)kAcc * np);
     ALLOC(S->d_grad, (size_t)6 * nv);

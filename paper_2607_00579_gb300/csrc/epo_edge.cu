@@ -122,11 +122,9 @@ constexpr int kAmbRun = 64;
 template <int MODE, int REC, int MAP, int REF>
 __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, double lam, float lamf) {
   const int p = en.p;
-  const int i = a.pair_src[p];
   const PairParam& P = a.pp[en.q];
-  // K64 holds fx, fy, cx, cy followed by 1/fx, 1/fy (refine scenes: at f0 (1 + gamma))
-  const double* Ki = a.K64 + 6 * (size_t)i;
-  const double* Kj = a.K64 + 6 * (size_t)a.pair_dst[p];
+  // the pair's projective form from the pair setup: (Y3 u', Y3 v', Y3) = z B (u, v, 1) + c
+  const double* Q = a.pp64 + kPP64 * (size_t)p + 12;
   double z = (double)en.z, u = (double)en.u, v = (double)en.v;
   if constexpr (REF) {  // the record's pixel, and Z0 alpha + beta in FP64 as the definition has it
     float u0, v0, z0;
@@ -135,27 +133,21 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, d
     v = (double)v0;
     z = fma((double)z0, (double)a.alpha[rec], (double)a.beta[rec]);
   }
-  const double xt = (u - Ki[2]) * Ki[4], yt = (v - Ki[3]) * Ki[5];
-  const double X[3] = {xt * z, yt * z, z};
-  const double* R = a.pp64 + 12 * (size_t)p;
-  double Y[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) Y[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + R[9 + r];
-  if (!(Y[2] > (double)a.eps_z)) return;
-  const double su = fma(Kj[0], Y[0], Kj[2] * Y[2]);  // Y3 u'
-  const double sv = fma(Kj[1], Y[1], Kj[3] * Y[2]);  // Y3 v'
-  if (!(su >= 0.0 && fma(-(double)(P.W - 1), Y[2], su) <= 0.0 && sv >= 0.0 &&
-        fma(-(double)(P.H - 1), Y[2], sv) <= 0.0))
+  const double Y3 = fma(z, fma(Q[6], u, fma(Q[7], v, Q[8])), Q[11]);
+  if (!(Y3 > (double)a.eps_z)) return;
+  const double su = fma(z, fma(Q[0], u, fma(Q[1], v, Q[2])), Q[9]);  // Y3 u'
+  const double sv = fma(z, fma(Q[3], u, fma(Q[4], v, Q[5])), Q[10]);  // Y3 v'
+  if (!(su >= 0.0 && fma(-(double)(P.W - 1), Y3, su) <= 0.0 && sv >= 0.0 && fma(-(double)(P.H - 1), Y3, sv) <= 0.0))
     return;
-  const float rz = rcp_approx((float)Y[2]);
+  const float rz = rcp_approx((float)Y3);
   int x0 = __float2int_rd((float)su * rz), y0 = __float2int_rd((float)sv * rz);
-  if (fma(-(double)x0, Y[2], su) < 0.0) --x0;
-  else if (fma(-(double)(x0 + 1), Y[2], su) >= 0.0) ++x0;
-  if (fma(-(double)y0, Y[2], sv) < 0.0) --y0;
-  else if (fma(-(double)(y0 + 1), Y[2], sv) >= 0.0) ++y0;
+  if (fma(-(double)x0, Y3, su) < 0.0) --x0;
+  else if (fma(-(double)(x0 + 1), Y3, su) >= 0.0) ++x0;
+  if (fma(-(double)y0, Y3, sv) < 0.0) --y0;
+  else if (fma(-(double)(y0 + 1), Y3, sv) >= 0.0) ++y0;
   x0 = min(x0, P.W - 2);  // the last cell is clamped (u' = W - 1 is in bounds)
   y0 = min(y0, P.H - 2);
-  const double sa = fma(-(double)x0, Y[2], su), sb = fma(-(double)y0, Y[2], sv);  // Y3 (u' - x0), Y3 (v' - y0)
+  const double sa = fma(-(double)x0, Y3, su), sb = fma(-(double)y0, Y3, sv);  // Y3 (u' - x0), Y3 (v' - y0)
   float f00, f01, f10, f11;
   taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, x0, y0, f00, f01, f10, f11);
   const float caf = (float)sa * rz, cbf = (float)sb * rz;  // relative error < 3e-7
@@ -168,7 +160,7 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, d
   if (fabsf(df - lamf) > tcl) {
     pass = df <= lamf;
   } else {  // near the clamp: decide on the FP64 value
-    const double iz = 1.0 / Y[2];
+    const double iz = 1.0 / Y3;
     const double ca = sa * iz, cb = sb * iz;
     const double d = (1.0 - ca) * (1.0 - cb) * f00 + ca * (1.0 - cb) * f01 + (1.0 - ca) * cb * f10 + ca * cb * f11;
     pass = d <= lam;
@@ -186,25 +178,26 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, d
   if constexpr (MODE != MODE_FWD) {
     const float drho = pass ? (fabsf(df) <= delta ? df : copysignf(delta, df)) : 0.f;
     if (drho != 0.f) {
-      const float y0f = (float)Y[0], y1f = (float)Y[1], y2f = (float)Y[2];
-      const float gx = drho * ddu * P.fx * rz;
-      const float gy = drho * ddv * P.fy * rz;
-      const float gz = -(gx * y0f + gy * y1f) * rz;
+      // the adjoint in the fast path's form, from the normalised coordinates (xn, yn) of u', v'
+      const float xn = ((float)su * rz - P.cx) / P.fx, yn = ((float)sv * rz - P.cy) / P.fy;
+      const float ga = drho * (P.fx * ddu), gb = drho * (P.fy * ddv), gc = -fmaf(ga, xn, gb * yn);
+      const float gx = ga * rz, gy = gb * rz, gz = gc * rz;
       atomicAdd(acc + 2, (double)gx);
       atomicAdd(acc + 3, (double)gy);
       atomicAdd(acc + 4, (double)gz);
-      atomicAdd(acc + 5, (double)(y1f * gz - y2f * gy));
-      atomicAdd(acc + 6, (double)(y2f * gx - y0f * gz));
-      atomicAdd(acc + 7, (double)(y0f * gy - y1f * gx));
+      atomicAdd(acc + 5, (double)fmaf(yn, gc, -gb));
+      atomicAdd(acc + 6, (double)fmaf(-xn, gc, ga));
+      atomicAdd(acc + 7, (double)fmaf(xn, gb, -(yn * ga)));
       if constexpr (REF) {
-        // R (x~, y~, 1) = dY/dz; dRho/dz = g . dY/dz; the focal terms as in the fast path
-        const float xtf = (float)xt, ytf = (float)yt, zf = (float)z;
+        // R (x~, y~, 1) = dY/dz; dRho/dz = g . dY/dz; the focal terms as in the fast path (the
+        // entry holds the record's unit-depth ray (x~, y~))
+        const float xtf = en.u, ytf = en.v, zf = (float)z;
         const float* r = P.r;
         const float dz = gx * fmaf(r[0], xtf, fmaf(r[1], ytf, r[2])) + gy * fmaf(r[3], xtf, fmaf(r[4], ytf, r[5])) +
                          gz * fmaf(r[6], xtf, fmaf(r[7], ytf, r[8]));
         const float gr2 = gx * r[2] + gy * r[5] + gz * r[8];
         atomicAdd(a.pair_facc + 2 * (size_t)p, (double)(zf * (gr2 - dz)));
-        atomicAdd(a.pair_facc + 2 * (size_t)p + 1, (double)(gx * y0f + gy * y1f));
+        atomicAdd(a.pair_facc + 2 * (size_t)p + 1, (double)(-gc));  // gx Y0 + gy Y1
         if constexpr (MODE == MODE_FUSED) a.dzr[P.dbase + rec] = dz;  // the fast path wrote 0
       }
     }

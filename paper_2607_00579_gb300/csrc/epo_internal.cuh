@@ -56,6 +56,11 @@ __device__ __forceinline__ void load_record(const void* base, int64_t idx, float
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// FP64 words per pair written by the pair setup: the relative pose R_ji (9), t_ji (3), and its
+// projective form B = K_j R_ji K_i^-1 (9), c = K_j t_ji (3), with which a record (u, v, z)
+// of view i lands at (Y3 u', Y3 v', Y3) = z B (u, v, 1) + c in view j
+constexpr int kPP64 = 24;
+
 constexpr int kAcc = 8;         // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
 constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)
 
@@ -117,7 +122,7 @@ struct EdgeArgs {
   const int32_t* pair_src;       // n_pairs
   const int32_t* pair_dst;       // n_pairs
   const PairParam* pp;           // n_pairs, in source-view pair-list order (index q)
-  const double* pp64;            // n_pairs x 12: R_ji (9), t_ji (3) in f64
+  const double* pp64;            // n_pairs x kPP64 (f64): R_ji (9), t_ji (3), B (9), c (3)
   const uint8_t* pair_active;    // n_pairs
   const unsigned long long* tex; // n_views texture objects (GATHER_TEX)
   double* pair_acc;              // n_pairs x kAcc

@@ -76,6 +76,27 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   const float t0 = __shfl_sync(0xffffffffu, vf, base + 9);
   const float t1 = __shfl_sync(0xffffffffu, vf, base + 10);
   const float t2 = __shfl_sync(0xffffffffu, vf, base + 11);
+  // the exact path's projective form (FP64): with M = R_ji K_i^-1, lane (r, c) < 9 forms
+  // B[r][c] = (K_j M)[r][c] and lane 9 + r forms c[r] = (K_j t_ji)[r]; K: fx, fy, cx, cy,
+  // 1/fx, 1/fy (refine scenes: at f0 (1 + gamma))
+  const double* K = a.refine ? a.K64r : a.K64;
+  const double* Ki = K + 6 * (size_t)i;
+  const double* Kj = K + 6 * (size_t)j;
+  const int rb = e < 9 ? e / 3 : 0, cb = e < 9 ? e % 3 : 0;
+  const double Rr0 = __shfl_sync(0xffffffffu, val, base + 3 * rb);      // R[r][0]
+  const double Rr1 = __shfl_sync(0xffffffffu, val, base + 3 * rb + 1);  // R[r][1]
+  double Mv = 0.0;
+  if (pv && e < 9)
+    Mv = cb == 0 ? val * Ki[4] : (cb == 1 ? val * Ki[5] : val - fma(Rr0, Ki[2] * Ki[4], Rr1 * (Ki[3] * Ki[5])));
+  const double M2c = __shfl_sync(0xffffffffu, Mv, base + 6 + cb);  // M[2][c]
+  const double t2d = __shfl_sync(0xffffffffu, val, base + 11);     // t_ji[2]
+  double Bv = 0.0;
+  if (pv && e < 12) {
+    const bool tcol = e >= 9;
+    const int r = tcol ? e - 9 : rb;
+    const double m = tcol ? val : Mv, m2 = tcol ? t2d : M2c;
+    Bv = r == 0 ? fma(Kj[0], m, Kj[2] * m2) : (r == 1 ? fma(Kj[1], m, Kj[3] * m2) : m);
+  }
   const bool bad = pv && e < 12 && !isfinite(val);
   if (__ballot_sync(0xffffffffu, bad)) {
     if (bad) atomicOr(a.flag, 1);  // a non-finite pose: the step must not update
@@ -84,7 +105,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   PairParam* out = a.pp + q;
   float* of = reinterpret_cast<float*>(out);
   if (e < 12) {
-    a.pp64[12 * (size_t)p + e] = val;  // R (9) then t (3), as in PairParam
+    a.pp64[kPP64 * (size_t)p + e] = val;  // R (9) then t (3), as in PairParam
+    a.pp64[kPP64 * (size_t)p + 12 + e] = Bv;  // B (9) then c (3)
     of[e] = vf;
   } else if (e == 15) {
     out->Et = 4.f * kU32 * (fabsf(t0) + fabsf(t1) + fabsf(t2));
@@ -210,7 +232,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         // the pair's sums (frame j), weight and relative pose are loaded together; a target
         // entry reads T_ji = I, so that both roles run the same instructions
         const double2* acc = reinterpret_cast<const double2*>(a.pair_acc + (size_t)kAcc * p);
-        const double2* Rt = reinterpret_cast<const double2*>(src ? a.pp64 + 12 * (size_t)p : kIdentityPose);
+        const double2* Rt = reinterpret_cast<const double2*>(src ? a.pp64 + kPP64 * (size_t)p : kIdentityPose);
         const double2 s01 = acc[0], s23 = acc[1], s45 = acc[2], s67 = acc[3];
         const double2 R01 = Rt[0], R23 = Rt[1], R45 = Rt[2], R67 = Rt[3], R8t0 = Rt[4], t12 = Rt[5];
         double c = a.pair_lw[p];  // the pair's weight in its scene's loss (0: not evaluated)
