@@ -85,18 +85,22 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
   const int rb = e < 9 ? e / 3 : 0, cb = e < 9 ? e % 3 : 0;
   const double Rr0 = __shfl_sync(0xffffffffu, val, base + 3 * rb);      // R[r][0]
   const double Rr1 = __shfl_sync(0xffffffffu, val, base + 3 * rb + 1);  // R[r][1]
-  double Mv = 0.0;
-  if (pv && e < 9)
-    Mv = cb == 0 ? val * Ki[4] : (cb == 1 ? val * Ki[5] : val - fma(Rr0, Ki[2] * Ki[4], Rr1 * (Ki[3] * Ki[5])));
+  // every lane runs the same FP64 instructions (selected operands, no divergent branches): on
+  // this GPU each FP64 warp instruction holds the sub-partition's FP64 pipe for many cycles
+  const double kx = pv ? Ki[2] * Ki[4] : 0.0, ky = pv ? Ki[3] * Ki[5] : 0.0;  // cx/fx, cy/fy of view i
+  // M[r][c] = R[r][c] s_c + o, s = (1/fx_i, 1/fy_i, 1), o = -(R[r][0] cx_i/fx_i + R[r][1] cy_i/fy_i) for c = 2
+  const double sc = cb == 0 ? (pv ? Ki[4] : 0.0) : (cb == 1 ? (pv ? Ki[5] : 0.0) : 1.0);
+  const double oc = -fma(Rr0, kx, Rr1 * ky);
+  const double Mv = fma(val, sc, cb == 2 ? oc : 0.0);
   const double M2c = __shfl_sync(0xffffffffu, Mv, base + 6 + cb);  // M[2][c]
   const double t2d = __shfl_sync(0xffffffffu, val, base + 11);     // t_ji[2]
-  double Bv = 0.0;
-  if (pv && e < 12) {
-    const bool tcol = e >= 9;
-    const int r = tcol ? e - 9 : rb;
-    const double m = tcol ? val : Mv, m2 = tcol ? t2d : M2c;
-    Bv = r == 0 ? fma(Kj[0], m, Kj[2] * m2) : (r == 1 ? fma(Kj[1], m, Kj[3] * m2) : m);
-  }
+  // B[r][c] = a_r M[r][c] + b_r M[2][c] and c[r] = a_r t[r] + b_r t[2], (a, b) = (fx_j, cx_j),
+  // (fy_j, cy_j), (1, 0) for r = 0, 1, 2
+  const bool tcol = e >= 9;
+  const int rrow = tcol ? (e < 12 ? e - 9 : 2) : rb;
+  const double fa = rrow == 0 ? (pv ? Kj[0] : 0.0) : (rrow == 1 ? (pv ? Kj[1] : 0.0) : 1.0);
+  const double fb = rrow == 0 ? (pv ? Kj[2] : 0.0) : (rrow == 1 ? (pv ? Kj[3] : 0.0) : 0.0);
+  const double Bv = fma(fa, tcol ? val : Mv, fb * (tcol ? t2d : M2c));
   const bool bad = pv && e < 12 && !isfinite(val);
   if (__ballot_sync(0xffffffffu, bad)) {
     if (bad) atomicOr(a.flag, 1);  // a non-finite pose: the step must not update
