@@ -4,19 +4,23 @@ loss + gradient edge kernel, FP64 finalize, FP64 Adam + Exp retraction (one CUDA
 replay).  Prints one JSON line.
 
 Workloads (--workload; seeded synthetic scenes, records and maps built on the fly):
-  ring32   (default) 32 views at 518x392 on a ring, each paired with its 8 nearest views
+  batch64  (default) 64 independent scenes (8..120 views, 256x192 / 518x392 / 518x518, 8
+           neighbours, 2-8 % edge density; 4,305 views, 34,440 pairs, 3.2e8 evaluations per
+           step) batched in one launch per stage, FP32 records and maps: the largest workload
+           at the paper's FP32 precision.  Adds the plain per-scene form (64 handles, kernels
+           launched one by one) at equal final pose accuracy.  --scenes N keeps the first N
+           scenes (a smaller case of the same kernel, for profiling).
+  ring32   32 views at 518x392 on a ring, each paired with its 8 nearest views
            (256 directed pairs), ~20,000 edge pixels per view, FP32 records and maps.
   walk200  200 views at 518x392 on a random walk, 10 neighbours (2,000 pairs), ~30,000 edge
            pixels per view (6e7 evaluations per step); adds the autograd forward + adjoint
            timing and the device memory against a stored-Jacobian variant.
-  batch64  64 independent scenes (8..120 views, 256x192 / 518x392 / 518x518, 8 neighbours,
-           2-8 % edge density) batched in one launch per stage; adds the plain per-scene form
-           (64 handles, kernels launched one by one) at equal final pose accuracy.
   ring500  500 views at 518x518, 12 neighbours (6,000 pairs), BF16 maps and FP16 depth;
            adds the FP32 form of the same scene and both forms' final pose errors.
 Metric: edge-pixel x pair evaluations per second of the loss + gradient step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+                  [--scenes N] [--schedule GATHER/BLOCK/RPT] [--no-legs] [--no-cpu-baseline]
 
 --impl reference times the FP64 CPU oracle (the reference arm for this build) on the host
 cores on the same workload and metric.  For N > 1 (torchrun) every rank runs an
@@ -54,7 +58,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ring32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
+    ap.add_argument("--scenes", type=int, default=0,
+                    help="batch64 only: keep the first N scenes (0 = all 64)")
+    ap.add_argument("--schedule", default="",
+                    help="fixed edge-kernel schedule gather/block/records_per_thread, e.g. tex/128/2 "
+                         "(default: autotuned)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the workload's comparison legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -69,16 +79,19 @@ def dist_env():
 class Workload:
     """Seeded synthetic scenes of one benchmark workload, with the stored dtypes."""
 
-    def __init__(self, key):
+    def __init__(self, key, n_scenes=0):
         import synth
         self.key = key
         self.name = WORKLOADS[key]
+        if key == "batch64" and n_scenes:
+            self.name = f"batch64_uneven_first{n_scenes}of64_8to120views_k8_f32"
         if key == "ring32":
             self.scenes = [synth.make_scene(synth.RING32_518x392, keep_depth=True)]
         elif key == "walk200":
             self.scenes = [synth.make_scene(synth.WALK200_518x392)]
         elif key == "batch64":
-            self.scenes = [synth.make_scene(sp) for sp in synth.batch64_uneven_specs()]
+            specs = synth.batch64_uneven_specs()
+            self.scenes = [synth.make_scene(sp) for sp in (specs[:n_scenes] if n_scenes else specs)]
         elif key == "ring500":
             self.scenes = [synth.make_scene(synth.RING500_518x518)]
         else:
@@ -174,23 +187,29 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def captured_traffic(workload, gather, block, rpt):
+def captured_traffic(workload, gather, block, rpt, evals):
     """DRAM bytes per edge-kernel launch from the committed ncu capture, or None when the
-    kernel source changed since the capture or this schedule was not captured."""
+    kernel source changed since the capture or this schedule was not captured.  A capture
+    of a smaller case of the same workload (its first scenes) is scaled to a full launch by
+    the evaluations it processed."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "edge_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    with open(os.path.join(ROOT, d["kernel_source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != d["kernel_source_sha256"]:
-            return None
-    if d.get("workload") != workload:
-        return None
-    key = f"{'tex' if gather == 2 else 'ldg'}/{block}/{rpt}"
-    v = d["dram_bytes_per_launch"].get(key)
-    return None if v is None else int(v)
+    key = f"{ {1: 'ldg', 2: 'tex', 3: 'mix'}.get(gather, '?') }/{block}/{rpt}"
+    for c in d.get("captures", []):
+        srcs = c["kernel_sources_sha256"]
+        ok = True
+        for path, sha in srcs.items():
+            with open(os.path.join(ROOT, path), "rb") as f:
+                ok = ok and hashlib.sha256(f.read()).hexdigest() == sha
+        if not ok or c.get("workload") != workload or key not in c["dram_bytes_per_launch"]:
+            continue
+        v = c["dram_bytes_per_launch"][key]
+        return int(round(v * evals / c["evals_per_launch"]))
+    return None
 
 
 # ------------------------------------------------------------------------------------------
@@ -298,7 +317,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = Workload(args.workload)
+    wl = Workload(args.workload, args.scenes)
     # each timed step is a bounded sample: a pair subset sized so that the run stays short
     per_step_budget = 150.0 / max(args.steps + args.warmup, 1)
     osc, T, fx, evals, n_pairs = oracle_sample(wl, per_step_budget)
@@ -367,7 +386,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     import paper_2607_00579_gb300 as epo
 
-    wl = Workload(args.workload)
+    wl = Workload(args.workload, args.scenes)
     stream = torch.cuda.current_stream()
     T_init = wl.T_init
     # distance transform fields built on the GPU by the library (construction step)
@@ -378,9 +397,17 @@ def run_ours(args):
     def scene(options, prts=parts, dt=(rd, md)):
         return epo.Scene(prts, record_dtype=dt[0], map_dtype=dt[1], options=options, on_device=True)
 
-    s = scene(epo.default_options(autotune=2, **lr))
-    s.set_poses(T_init)
-    s.autotune()
+    if args.schedule:
+        g, b, r = args.schedule.split("/")
+        fixed = dict(gather={"ldg": epo.EPO_GATHER_LDG, "tex": epo.EPO_GATHER_TEX, "mix": epo.EPO_GATHER_MIX}[g],
+                     block_threads=int(b),
+                     records_per_thread=int(r))
+        s = scene(epo.default_options(**lr, **fixed))
+        s.set_poses(T_init)
+    else:
+        s = scene(epo.default_options(autotune=2, **lr))
+        s.set_poses(T_init)
+        s.autotune()
     info = s.info()
     evals = info.evals_per_step
     # a second handle on the same workload and schedule, with CUDA events captured around
@@ -451,20 +478,12 @@ def run_ours(args):
            "h2d_bytes_per_step": int(T_host.numel() * 8),
            "d2h_bytes_per_step": int(T_out.numel() * 8 + loss_out.numel() * 8 + 8)}  # + the status word
 
-    # roofline of the dominant kernel (fused loss + gradient edge kernel): the four taps of
-    # every evaluation, plus every record once per step (shared by its view's pairs)
+    # roofline of the dominant kernel (fused loss + gradient edge kernel)
     peak, peak_src = measured_peaks()
-    s_map = 2 if wl.mixed else 4
-    s_rec = 8 if wl.mixed else 16
-    alg_bytes = evals * 4 * s_map + info.n_records * s_rec
     kern_avg = float(np.mean(kern_ms))
-    achieved = alg_bytes / (kern_avg * 1e-3) / 1e9
-    traffic = captured_traffic(wl.name, info.gather, info.block_threads, info.records_per_thread)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-            "kernel": "k_edge (fused loss + gradient)", "kernel_ms": kern_avg,
-            "bytes_per_eval": alg_bytes / evals, "algorithmic_bytes_per_launch": alg_bytes}
+    traffic = captured_traffic(wl.name, info.gather, info.block_threads, info.records_per_thread, evals)
     gather_roof = gather_roofline(epo, wl, info, evals, kern_avg, peak)
+    roof = roofline_line(wl, info, evals, kern_avg, gather_roof, traffic, peak, peak_src)
     st_avg = np.mean(np.array(stages), axis=0)
     queued, overflow = epo._binding.epo_fixup_stats(st_.handle)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -486,7 +505,9 @@ def run_ours(args):
             "exact_fixup_samples": queued, "exact_fixup_overflow": overflow,
             "wall_ms_per_step": 1e3 * t_wall / args.steps}
     del st_
-    if wl.key == "walk200":
+    if args.no_legs:
+        pass
+    elif wl.key == "walk200":
         line["autograd"] = autograd_leg(epo, torch, s, T_init, evals, args, flush_l2, stream)
     elif wl.key == "batch64":
         leg = plain_per_scene_leg(epo, torch, wl, s, parts, (rd, md), lr, evals, args, flush_l2, stream)
@@ -507,6 +528,36 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def roofline_line(wl, info, evals, kern_ms, gr, traffic, hbm_peak, peak_src):
+    """The edge kernel against its roofline t_roof = max(t_hbm, t_gather) (gather_roofline).
+    The bound is the larger term: "gather" when serving one 2x2 footprint per evaluation at the
+    best rate this GPU's gather probe measured takes longer than moving the compulsory bytes
+    (records and maps once) at the measured HBM bandwidth, else "hbm".  achieved and peak are
+    the gather term's tap bytes (4 s_map per evaluation) per second: the kernel's, and the
+    probe's; frac = t_roof / kernel time.  The HBM side is reported beside it: the compulsory
+    bytes, their time at the measured peak, and the DRAM bytes ncu counted for the kernel."""
+    s_map = 2 if wl.mixed else 4
+    tap = 4 * s_map
+    probe = max(gr["gather_footprints_per_s"].values())
+    bound = "gather" if gr["t_gather_ms"] >= gr["t_hbm_ms"] else "hbm"
+    if bound == "gather":
+        achieved, peak, unit = evals * tap / (kern_ms * 1e-3) / 1e9, probe * tap / 1e9, "GB/s"
+        psrc = (f"measured in this run: best 2x2-footprint rate of epo_gather_probe "
+                f"({probe / 1e9:.1f} G footprints/s x {tap} B of taps)")
+    else:
+        achieved, peak, unit = gr["hbm_compulsory_bytes"] / (kern_ms * 1e-3) / 1e9, hbm_peak, "GB/s"
+        psrc = f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": gr["t_roof_ms"] / kern_ms,
+            "traffic": traffic, "peak_source": psrc, "kernel": "k_edge (fused loss + gradient)",
+            "kernel_ms": kern_ms, "t_roof_ms": gr["t_roof_ms"], "tap_bytes_per_eval": tap,
+            "hbm": {"compulsory_bytes": gr["hbm_compulsory_bytes"], "t_ms": gr["t_hbm_ms"],
+                    "peak_gbs": hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "compulsory_frac_of_kernel_time": gr["t_hbm_ms"] / kern_ms,
+                    "dram_gbs_of_traffic": None if traffic is None else traffic / (kern_ms * 1e-3) / 1e9,
+                    "dram_frac": None if traffic is None else traffic / (kern_ms * 1e-3) / 1e9 / hbm_peak,
+                    "traffic_over_compulsory": None if traffic is None else traffic / gr["hbm_compulsory_bytes"]}}
 
 
 def gather_roofline(epo, wl, info, evals, kern_ms, hbm_peak):

@@ -67,8 +67,10 @@ enum { EPO_POSE_SE3 = 0, EPO_POSE_MLP = 1 };
 #define EPO_POSE_MLP_PARAMS 69260
 /* Per-direction normaliser: sum(valid) (Algorithm 3) or |E_i| (Eq. 7). */
 enum { EPO_NORM_VALID = 0, EPO_NORM_ALL = 1 };
-/* How the kernels read the 2x2 map footprint: plain loads or texture gather. */
-enum { EPO_GATHER_AUTO = 0, EPO_GATHER_LDG = 1, EPO_GATHER_TEX = 2 };
+/* How the kernels read the 2x2 map footprint: plain loads, texture gather, or (pose-only
+ * scenes, two or more records per thread) the two side by side: of the two samples a thread
+ * has in flight, one through each path. */
+enum { EPO_GATHER_AUTO = 0, EPO_GATHER_LDG = 1, EPO_GATHER_TEX = 2, EPO_GATHER_MIX = 3 };
 
 typedef struct epo_scene* epo_scene_t;
 
@@ -109,7 +111,8 @@ typedef struct {
                                 2: the same, each timed launch starting from a cold L2 */
   int32_t gather;            /* EPO_GATHER_* (AUTO = LDG unless autotuned) */
   int32_t block_threads;     /* 0 = default (256); else 64..512, multiple of 32 */
-  int32_t records_per_thread;/* 0 = default (2); 1, 2 or 4 (two in flight at a time) */
+  int32_t records_per_thread;/* 0 = default (2); 1, 2, 4 or 8 (two in flight at a time;
+                                refine scenes: 2) */
   int32_t grid_blocks;       /* 0 = default (persistent: SMs x resident blocks) */
   int32_t timing;            /* 1: bracket the edge kernel with CUDA events (epo_kernel_time) */
   int32_t tail_pairs;        /* work items of the last wave (as many as the grid has blocks):
@@ -265,6 +268,23 @@ epo_status epo_step_plain(epo_scene_t scene, int32_t n_steps);
 /* Synchronise and report a pending numeric flag (and clear it). */
 epo_status epo_check(epo_scene_t scene);
 
+/* Bounded host waits (failure detection; no counterpart in the paper).  With
+ * seconds > 0, the calls that wait for the GPU on behalf of host outputs
+ * (epo_step, epo_step_host, epo_check, epo_loss_and_grad, epo_last_loss,
+ * epo_get_poses) poll the completion of the work they queued for at most
+ * that long, then return EPO_ERR_TIMEOUT instead of blocking.  The queued
+ * work is not cancelled: it runs to completion, the handle stays usable, and
+ * the next call that needs it (any of the calls above) waits for it first,
+ * within the same limit.  A call that ran out has not written its host
+ * outputs; the device state it advanced (poses and optimiser state of the
+ * steps it queued) is read back by epo_get_poses / epo_get_state once the
+ * work has finished.  Host outputs go through pinned staging owned by the
+ * scene, so nothing is written into caller memory after a call returns.
+ * seconds = 0 (the default) waits without a limit.  Other synchronising calls
+ * wait without a limit.  EPO_ERR_INVALID_ARG for a negative or non-finite
+ * limit. */
+epo_status epo_set_wait_limit(epo_scene_t scene, double seconds);
+
 /* Loss per scene (host, n_scenes doubles) computed by the most recent
  * evaluation or step (a step evaluates before it updates).  Synchronises. */
 epo_status epo_last_loss(epo_scene_t scene, double* loss);
@@ -416,9 +436,15 @@ epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dt
  * left-perturbation pose gradient, EPO_F32 records and FP32 maps) for one
  * scene, with every projection and branch decision taken in FP64.  The
  * intermediate per-pair sums live in one file-scope device array of the
- * library of fixed size, about 0.9 MB, which every GPU that loads the
- * library reserves until the process exits.  Hence the limits below:
- * larger problems are rejected with EPO_ERR_TOO_LARGE before any work.
+ * library of fixed size: EPO_NOALLOC_MAX_PAIRS x 21 doubles = 688,128
+ * bytes (672 KiB), which every GPU that loads the library reserves until
+ * the process exits.  Hence the limits below: larger problems are rejected
+ * with EPO_ERR_TOO_LARGE before any work.
+ *
+ *   - Records whose depth is not positive and finite are not part of the
+ *     problem, as at scene creation: they are never valid samples, and
+ *     under EPO_NORM_ALL the denominator |E_i| counts only the other
+ *     records of view i.
  *
  *   - The first call on a device looks up that array's device address (with
  *     the device current) and keeps it; make that first call before any
@@ -429,9 +455,11 @@ epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dt
  *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating
  *     library routine, on the device or the host.
  *   - Stream-ordered on cuda_stream; it does not synchronise.  Status codes:
- *     EPO_ERR_INVALID_ARG for a NULL pointer, no view or pair, or an invalid
- *     lambda / huber_delta / eps_z / norm_mode; EPO_ERR_TOO_LARGE beyond the
- *     limits; EPO_ERR_CUDA if a launch fails.  Indices and sizes inside the
+ *     EPO_ERR_INVALID_ARG for a NULL pointer, a pointer not aligned to its
+ *     element (records to 16 bytes), no view or pair, or an invalid lambda /
+ *     huber_delta / eps_z / norm_mode; EPO_ERR_TOO_LARGE beyond the limits
+ *     (views, pairs, or more than 2^31 - 1 tiles of 256 records in one
+ *     view); EPO_ERR_CUDA if a launch fails.  Indices and sizes inside the
  *     device buffers are not checked: they must be consistent.
  * ------------------------------------------------------------------------ */
 #define EPO_NOALLOC_MAX_VIEWS 1024
@@ -439,7 +467,7 @@ epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dt
 
 typedef struct {
   int32_t n_views, n_pairs;      /* 1..EPO_NOALLOC_MAX_VIEWS, 1..EPO_NOALLOC_MAX_PAIRS */
-  const float* records;          /* device, 16-byte aligned: {u, v, z, 0} per record, z > 0 finite */
+  const float* records;          /* device, 16-byte aligned: {u, v, z, 0} per record */
   const int64_t* rec_off;        /* device: n_views + 1 record offsets, view-major */
   int64_t max_records_per_view;  /* host value: the largest rec_off[i+1] - rec_off[i] */
   const float* maps;             /* device: every view's map, H rows of W floats, dense */

@@ -79,8 +79,6 @@ static void edt_1d(const double* f, int n, double* d, int* v, double* z) {
   }
 }
 
-/* dist[y*W + x] = Euclidean distance from pixel (x, y) to the nearest edge
- * pixel; a view without edges gets W + H everywhere. */
 /* Number of OpenMP threads the loss and gradient use (n > 0 sets it); returns the count in
  * effect.  Timing aid for the CPU baseline: one thread against all cores. */
 int oracle_set_threads(int n) {
@@ -93,6 +91,8 @@ int oracle_set_threads(int n) {
 #endif
 }
 
+/* dist[y*W + x] = Euclidean distance from pixel (x, y) to the nearest edge
+ * pixel; a view without edges gets W + H everywhere. */
 int oracle_edt(const uint8_t* edge, int W, int H, double* dist) {
   if (W < 1 || H < 1) return ORACLE_EINVAL;
   int any = 0;

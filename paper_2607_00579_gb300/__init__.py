@@ -15,16 +15,17 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 from . import _binding as B
-from ._binding import (EPO_BF16, EPO_F16, EPO_F32, EPO_GATHER_AUTO, EPO_GATHER_LDG, EPO_GATHER_TEX,
+from ._binding import (EPO_BF16, EPO_F16, EPO_F32, EPO_GATHER_AUTO, EPO_GATHER_LDG, EPO_GATHER_MIX, EPO_GATHER_TEX,
                        EPO_NORM_ALL, EPO_NORM_VALID, EpoError, default_options)
 
 __all__ = ["Scene", "EdgeLoss", "distance_field", "round_bf16", "default_options", "EpoError",
            "EPO_F32", "EPO_F16", "EPO_BF16", "EPO_NORM_VALID", "EPO_NORM_ALL", "EPO_GATHER_AUTO",
-           "EPO_GATHER_LDG", "EPO_GATHER_TEX", "library_path"]
+           "EPO_GATHER_LDG", "EPO_GATHER_TEX", "EPO_GATHER_MIX", "library_path"]
 
 
 def library_path() -> str:
-    return B.LIB_PATH
+    import os
+    return os.environ.get("EPO_LIBRARY") or B.LIB_PATH
 
 
 def _current_stream() -> int:

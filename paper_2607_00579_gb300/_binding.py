@@ -28,7 +28,7 @@ EPO_NOALLOC_MAX_PAIRS = 4096
 
 EPO_F32, EPO_F16, EPO_BF16 = 0, 1, 2
 EPO_NORM_VALID, EPO_NORM_ALL = 0, 1
-EPO_GATHER_AUTO, EPO_GATHER_LDG, EPO_GATHER_TEX = 0, 1, 2
+EPO_GATHER_AUTO, EPO_GATHER_LDG, EPO_GATHER_TEX, EPO_GATHER_MIX = 0, 1, 2, 3
 
 # Every symbol declared in include/epo.h (checked by the test-suite).
 EXPORTED = [
@@ -41,6 +41,7 @@ EXPORTED = [
     "epo_loss_and_grad_noalloc", "epo_gather_probe", "epo_set_refinement", "epo_refine_loss_and_grad",
     "epo_get_pair_active", "epo_get_schedule", "epo_build_viewgraph", "epo_get_refinement",
     "epo_set_pose_mlp", "epo_get_pose_mlp", "epo_get_pose_mlp_moments", "epo_step_host",
+    "epo_set_wait_limit",
 ]
 
 
@@ -105,16 +106,18 @@ _lib = None
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libepo.so (building it with nvcc first if it is missing or stale)."""
+    """Load libepo.so (building it with nvcc first if it is missing or stale), or the build
+    that the environment variable EPO_LIBRARY names (a variant built by build.py --out)."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing:
+    path = os.environ.get("EPO_LIBRARY") or LIB_PATH
+    if build_if_missing and path == LIB_PATH:
         from . import build as _b
         _b.build()
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libepo.so not built at {LIB_PATH}")
-    lib = ctypes.CDLL(LIB_PATH)
+    if not os.path.exists(path):
+        raise ImportError(f"libepo.so not built at {path}")
+    lib = ctypes.CDLL(path)
     P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     S = ctypes.c_void_p  # epo_scene_t
     sig = {
@@ -142,6 +145,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "epo_step_async": (I32, [S, I32]),
         "epo_step_plain": (I32, [S, I32]),
         "epo_check": (I32, [S]),
+        "epo_set_wait_limit": (I32, [S, D]),
         "epo_set_pair_subset": (I32, [S, I32, P]),
         "epo_autotune": (I32, [S]),
         "epo_distance_field": (I32, [P, I32, I32, P, P]),
@@ -240,6 +244,7 @@ def epo_step(scene, n): _call("epo_step", scene, ctypes.c_int32(n))
 def epo_step_async(scene, n): _call("epo_step_async", scene, ctypes.c_int32(n))
 def epo_step_plain(scene, n): _call("epo_step_plain", scene, ctypes.c_int32(n))
 def epo_check(scene): _call("epo_check", scene)
+def epo_set_wait_limit(scene, seconds: float): _call("epo_set_wait_limit", scene, float(seconds))
 def epo_autotune(scene): _call("epo_autotune", scene)
 def epo_last_loss(scene, loss): _call("epo_last_loss", scene, _ptr(loss))
 

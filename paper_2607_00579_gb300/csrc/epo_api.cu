@@ -9,8 +9,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/epo.h"
@@ -144,6 +146,15 @@ struct epo_scene {
   int32_t pose_stride = 1;
   std::vector<int32_t> pose_off, pose_ref;  // (pair, role) entries of every pose, pose-major
   int32_t* h_flag = nullptr;  // pinned
+  // host outputs go through pinned staging, so that a wait for them can be bounded:
+  // h_out = [loss (n_scenes) | gradient (6 n_views) | poses (12 n_views)]
+  double* h_out = nullptr;
+  // bounded host waits (epo_set_wait_limit): 0 = wait without limit; ev_wait marks the work a
+  // wait that ran out left queued (wait_pending), which the next call that reuses the staging
+  // waits for first
+  double wait_limit_s = 0.0;
+  cudaEvent_t ev_wait = nullptr;
+  bool wait_pending = false;
   double* d_io = nullptr;     // [poses (12 n_views) | loss (n_scenes) | flag (one word)]
   // epo_step_host's staging, pinned and mapped: h_in the input poses (12 n_views), h_io the
   // layout of d_io; dh_in, dh_io are their device addresses, read and written by the step's graph
@@ -184,6 +195,45 @@ epo_status cuda_fail(epo_scene* s, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                             \
     if (e_ != cudaSuccess) return cuda_fail(S, e_, #call); \
   } while (0)
+
+// Waits until the work queued before ev_wait has finished: without a limit by blocking on
+// the event, with one by polling it until the limit runs out (EPO_ERR_TIMEOUT; the work stays
+// queued, the handle stays usable, and the next call that needs it waits for it first).
+epo_status poll_pending(epo_scene* S) {
+  if (S->wait_limit_s <= 0.0) {
+    cudaError_t e = cudaEventSynchronize(S->ev_wait);
+    if (e != cudaSuccess) return cuda_fail(S, e, "cudaEventSynchronize");
+    S->wait_pending = false;
+    return EPO_OK;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(S->ev_wait);
+    if (e == cudaSuccess) {
+      S->wait_pending = false;
+      return EPO_OK;
+    }
+    if (e != cudaErrorNotReady) return cuda_fail(S, e, "cudaEventQuery");
+    const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (waited >= S->wait_limit_s)
+      return fail(S, EPO_ERR_TIMEOUT,
+                  "the wait limit of " + std::to_string(S->wait_limit_s) +
+                      " s ran out; the queued work continues and the next call waits for it");
+    std::this_thread::yield();
+  }
+}
+
+// Waits for everything queued on the scene's stream so far (see poll_pending).
+epo_status host_wait(epo_scene* S) {
+  cudaError_t e = cudaEventRecord(S->ev_wait, S->stream);
+  if (e != cudaSuccess) return cuda_fail(S, e, "cudaEventRecord");
+  S->wait_pending = true;
+  return poll_pending(S);
+}
+
+// Before a call reuses host staging that work left queued by a timed-out wait may still read
+// or write: wait for that work (within the limit).
+epo_status drain(epo_scene* S) { return S->wait_pending ? poll_pending(S) : EPO_OK; }
 
 template <typename T>
 epo_status dalloc(epo_scene* S, T** p, size_t count) {
@@ -506,6 +556,8 @@ epo_status mark(epo_scene* S, int k, cudaStream_t s) {
 epo_status run_edge(epo_scene* S, int mode, int gather, int rpt, int block, int tail, cudaStream_t s) {
   if (!schedule_fits(S, rpt, block))
     return fail(S, EPO_ERR_INVALID_ARG, "schedule needs more shared memory than a block has");
+  if (gather == GATHER_MIX && (S->refine || rpt == 1))
+    return fail(S, EPO_ERR_INVALID_ARG, "the mixed gather needs a pose-only scene and two or more records per thread");
   epo_status st = build_tiles(S, gather, rpt, block, tail);
   if (st != EPO_OK) return st;
   EdgeArgs ea = edge_args(S);
@@ -627,10 +679,12 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
   if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
     return fail(nullptr, EPO_ERR_INVALID_ARG, "block_threads must be 64..512, a multiple of 32");
   if (o.records_per_thread != 0 && o.records_per_thread != 1 && o.records_per_thread != 2 &&
-      o.records_per_thread != 4)
-    return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 1, 2 or 4");
-  if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_TEX)
+      o.records_per_thread != 4 && o.records_per_thread != 8)
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "records_per_thread must be 1, 2, 4 or 8");
+  if (o.gather < EPO_GATHER_AUTO || o.gather > EPO_GATHER_MIX)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "unknown gather mode");
+  if (o.gather == EPO_GATHER_MIX && (o.refine || o.records_per_thread == 1))
+    return fail(nullptr, EPO_ERR_INVALID_ARG, "EPO_GATHER_MIX needs a pose-only scene and two or more records per thread");
   if (o.tail_pairs == INT_MIN) return fail(nullptr, EPO_ERR_INVALID_ARG, "tail_pairs out of range");
   if (o.refine != 0 && o.refine != 1) return fail(nullptr, EPO_ERR_INVALID_ARG, "refine must be 0 or 1");
   if (o.pair_budget < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "pair_budget must be >= 0");
@@ -940,6 +994,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       for (const ViewDev& w : S->views) S->max_view_records = std::max(S->max_view_records, w.n_rec);
     }
     CK(cudaMallocHost(&S->h_flag, sizeof(int32_t)));
+    CK(cudaMallocHost(&S->h_out, ((size_t)n_scenes + 18 * nv) * 8));
+    CK(cudaEventCreateWithFlags(&S->ev_wait, cudaEventDisableTiming));
     CK(cudaHostAlloc(&S->h_io, ((size_t)12 * nv + n_scenes + 1) * 8, cudaHostAllocMapped));
     CK(cudaHostAlloc(&S->h_in, (size_t)12 * nv * 8, cudaHostAllocMapped));
     memset(S->h_io, 0, ((size_t)12 * nv + n_scenes + 1) * 8);
@@ -1079,6 +1135,19 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
         q.W = vj.W; q.H = vj.H; q.pitch = vj.pitch;
         q.map_off = vj.map_off;
         q.tex = th[S->pair_dst[p]];
+        // the pose-only kernel's bound: with |xn| <= max(cx + 1, W - cx) / fx for a sample
+        // within one pixel of the image, |du'| <= fx |1/Y3| E (1 + |xn|) x 2 (safety) + cu,
+        // and the same for v'; Gb = 1/8 / (fx + fy + W + H) keeps t below 1/4 + cb there and,
+        // for a sample farther out, below its distance to the image
+        const double bu = (double)vj.fx + std::max((double)vj.cx + 1.0, (double)vj.W - (double)vj.cx);
+        const double bv = (double)vj.fy + std::max((double)vj.cy + 1.0, (double)vj.H - (double)vj.cy);
+        q.Kb = (float)(2.0 * std::max(bu, bv) * (1.0 + 1e-6));
+        q.cb = std::max(q.cu, q.cv);
+        q.Gb = (float)(0.125 / ((double)vj.fx + (double)vj.fy + (double)vj.W + (double)vj.H));
+        q.Wm2 = (float)(vj.W - 2);
+        q.Hm2 = (float)(vj.H - 2);
+        q.Wf = (float)vj.W;
+        q.Hf = (float)vj.H;
       }
       if (S->refine) {  // each pair's block of d(rho)/dz values, one per source record
         int64_t run = 0;
@@ -1101,7 +1170,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     // schedule
     S->block = o.block_threads ? o.block_threads : 256;
     S->rpt = o.records_per_thread ? o.records_per_thread : 2;
-    S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : GATHER_LDG;
+    S->gather = o.gather == EPO_GATHER_TEX ? GATHER_TEX : (o.gather == EPO_GATHER_MIX ? GATHER_MIX : GATHER_LDG);
     if (!schedule_fits(S, S->rpt, S->block)) S->block = 128;
     S->tail = o.tail_pairs == -1 ? 0 : o.tail_pairs;
     epo_status bs = build_tiles(S);
@@ -1126,6 +1195,8 @@ void destroy_impl(epo_scene* S) {
   for (auto& b : S->bufs)
     if (b.p) cudaFree(b.p);
   if (S->h_flag) cudaFreeHost(S->h_flag);
+  if (S->h_out) cudaFreeHost(S->h_out);
+  if (S->ev_wait) cudaEventDestroy(S->ev_wait);
   if (S->h_io) cudaFreeHost(S->h_io);
   if (S->h_in) cudaFreeHost(S->h_in);
   if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
@@ -1170,11 +1241,13 @@ int32_t epo_abi_version(void) { return EPO_ABI_VERSION; }
 
 epo_status epo_create_scene(const epo_scene_desc* desc, const epo_options* opts, void* cuda_stream,
                             epo_scene_t* out) {
+  EPO_RANGE("epo_create_scene");
   return epo_create_batch(1, desc, opts, cuda_stream, out);
 }
 
 epo_status epo_create_batch(int32_t n_scenes, const epo_scene_desc* descs, const epo_options* opts,
                             void* cuda_stream, epo_scene_t* out) {
+  EPO_RANGE("epo_create_batch");
   if (out) *out = nullptr;
   epo_scene* S = new (std::nothrow) epo_scene();
   if (!S) return fail(nullptr, EPO_ERR_OOM, "host allocation failed");
@@ -1188,6 +1261,7 @@ epo_status epo_create_batch(int32_t n_scenes, const epo_scene_desc* descs, const
 }
 
 void epo_destroy_scene(epo_scene_t S) {
+  EPO_RANGE("epo_destroy_scene");
   if (S) cudaStreamSynchronize(S->stream);
   destroy_impl(S);
 }
@@ -1195,6 +1269,7 @@ void epo_destroy_scene(epo_scene_t S) {
 const char* epo_last_error(epo_scene_t S) { return S ? S->err.c_str() : g_create_error.c_str(); }
 
 epo_status epo_scene_info_get(epo_scene_t S, epo_scene_info* info) {
+  EPO_RANGE("epo_scene_info_get");
   if (!S || !info) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   info->n_scenes = S->n_scenes;
   info->n_views = S->n_views;
@@ -1255,6 +1330,7 @@ static epo_status set_mlp_scale(epo_scene* S, const double* T) {
 }
 
 epo_status epo_set_poses(epo_scene_t S, const double* T) {
+  EPO_RANGE("epo_set_poses");
   if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   for (int64_t k = 0; k < 12 * (int64_t)S->n_views; ++k)
     if (!isfinite(T[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
@@ -1272,6 +1348,7 @@ epo_status epo_set_poses(epo_scene_t S, const double* T) {
 }
 
 epo_status epo_set_pose_mlp(epo_scene_t S, const float* params) {
+  EPO_RANGE("epo_set_pose_mlp");
   if (!S || !params) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
   const size_t n = (size_t)S->n_scenes * kMlpParams, nv = (size_t)S->n_views;
@@ -1287,6 +1364,7 @@ epo_status epo_set_pose_mlp(epo_scene_t S, const float* params) {
 }
 
 epo_status epo_get_pose_mlp_moments(epo_scene_t S, float* m, float* v, float* dm, float* dv) {
+  EPO_RANGE("epo_get_pose_mlp_moments");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
   const size_t n = (size_t)S->n_scenes * kMlpParams * 4, nd = 12 * (size_t)S->n_views;
@@ -1299,6 +1377,7 @@ epo_status epo_get_pose_mlp_moments(epo_scene_t S, float* m, float* v, float* dm
 }
 
 epo_status epo_get_pose_mlp(epo_scene_t S, float* params, float* delta) {
+  EPO_RANGE("epo_get_pose_mlp");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (!S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.pose_param = EPO_POSE_MLP");
   if (params)
@@ -1309,13 +1388,21 @@ epo_status epo_get_pose_mlp(epo_scene_t S, float* params, float* delta) {
 }
 
 epo_status epo_get_poses(epo_scene_t S, double* T) {
+  EPO_RANGE("epo_get_poses");
   if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
-  CK(cudaMemcpyAsync(T, S->d_T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
-  CK(cudaStreamSynchronize(S->stream));
+  epo_status st = drain(S);
+  if (st != EPO_OK) return st;
+  const size_t nv = (size_t)S->n_views;
+  double* hp = S->h_out + S->n_scenes + 6 * nv;
+  CK(cudaMemcpyAsync(hp, S->d_T, 12 * nv * 8, cudaMemcpyDeviceToHost, S->stream));
+  st = host_wait(S);
+  if (st != EPO_OK) return st;
+  memcpy(T, hp, 12 * nv * 8);
   return EPO_OK;
 }
 
 epo_status epo_set_poses_dev(epo_scene_t S, const double* T) {
+  EPO_RANGE("epo_set_poses_dev");
   if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(S->d_T, T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
   if (S->pose_mlp) {  // as epo_set_poses: P^0, offsets cleared, poses recomputed
@@ -1333,12 +1420,14 @@ epo_status epo_set_poses_dev(epo_scene_t S, const double* T) {
 }
 
 epo_status epo_get_poses_dev(epo_scene_t S, double* T) {
+  EPO_RANGE("epo_get_poses_dev");
   if (!S || !T) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(T, S->d_T, 12 * (size_t)S->n_views * 8, cudaMemcpyDeviceToDevice, S->stream));
   return EPO_OK;
 }
 
 epo_status epo_get_state(epo_scene_t S, int64_t* step, double* m, double* v) {
+  EPO_RANGE("epo_get_state");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (step) CK(cudaMemcpyAsync(step, S->d_step, 8, cudaMemcpyDeviceToHost, S->stream));
   if (m) CK(cudaMemcpyAsync(m, S->d_m, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
@@ -1348,6 +1437,7 @@ epo_status epo_get_state(epo_scene_t S, int64_t* step, double* m, double* v) {
 }
 
 epo_status epo_set_state(epo_scene_t S, int64_t step, const double* m, const double* v) {
+  EPO_RANGE("epo_set_state");
   if (!S || step < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step");
   CK(cudaMemcpyAsync(S->d_step, &step, 8, cudaMemcpyHostToDevice, S->stream));
   if (m) CK(cudaMemcpyAsync(S->d_m, m, 6 * (size_t)S->n_views * 8, cudaMemcpyHostToDevice, S->stream));
@@ -1361,6 +1451,7 @@ epo_status epo_set_state(epo_scene_t S, int64_t step, const double* m, const dou
 }
 
 epo_status epo_loss_and_grad_dev(epo_scene_t S, double* loss_dev, double* grad_dev) {
+  EPO_RANGE("epo_loss_and_grad_dev");
   if (!S || !loss_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
@@ -1373,24 +1464,33 @@ epo_status epo_loss_and_grad_dev(epo_scene_t S, double* loss_dev, double* grad_d
 }
 
 epo_status epo_loss_and_grad(epo_scene_t S, double* loss, double* grad) {
+  EPO_RANGE("epo_loss_and_grad");
   if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
-  epo_status st = maybe_autotune(S);
+  epo_status st = drain(S);
+  if (st != EPO_OK) return st;
+  st = maybe_autotune(S);
   if (st != EPO_OK) return st;
   st = enqueue_loss_grad(S, S->stream, S->d_T);
   if (st != EPO_OK) return st;
-  CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, S->stream));
-  if (grad) CK(cudaMemcpyAsync(grad, S->d_grad, 6 * (size_t)S->n_views * 8, cudaMemcpyDeviceToHost, S->stream));
+  const size_t ns = (size_t)S->n_scenes, nv = (size_t)S->n_views;
+  CK(cudaMemcpyAsync(S->h_out, S->d_loss, ns * 8, cudaMemcpyDeviceToHost, S->stream));
+  if (grad) CK(cudaMemcpyAsync(S->h_out + ns, S->d_grad, 6 * nv * 8, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, S->stream));
-  CK(cudaStreamSynchronize(S->stream));
+  st = host_wait(S);
+  if (st != EPO_OK) return st;
+  memcpy(loss, S->h_out, ns * 8);
+  if (grad) memcpy(grad, S->h_out + ns, 6 * nv * 8);
   if (*S->h_flag & 1) {
     CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    CK(cudaStreamSynchronize(S->stream));
+    st = host_wait(S);
+    if (st != EPO_OK) return st;
     return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient");
   }
   return EPO_OK;
 }
 
 epo_status epo_pair_stats(epo_scene_t S, double* stats) {
+  EPO_RANGE("epo_pair_stats");
   if (!S || !stats) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(stats, S->d_pair_acc, (size_t)kAcc * S->n_pairs * 8, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
@@ -1398,6 +1498,7 @@ epo_status epo_pair_stats(epo_scene_t S, double* stats) {
 }
 
 epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev) {
+  EPO_RANGE("epo_forward_dev");
   if (!S || !loss_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
@@ -1418,6 +1519,7 @@ epo_status epo_forward_dev(epo_scene_t S, const double* xi_dev, double* loss_dev
 
 epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* dloss_dev,
                             double* grad_xi_dev) {
+  EPO_RANGE("epo_backward_dev");
   if (!S || !dloss_dev || !grad_xi_dev) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(launch_twist_poses(S->d_T, xi_dev, S->d_T_eval, S->n_views, S->stream));
   StepArgs a = step_args(S, S->d_T_eval, dloss_dev);
@@ -1435,6 +1537,7 @@ epo_status epo_backward_dev(epo_scene_t S, const double* xi_dev, const double* d
 }
 
 epo_status epo_step_async(epo_scene_t S, int32_t n_steps) {
+  EPO_RANGE("epo_step_async");
   if (!S || n_steps < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step count");
   epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
@@ -1445,6 +1548,7 @@ epo_status epo_step_async(epo_scene_t S, int32_t n_steps) {
 }
 
 epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, double* loss) {
+  EPO_RANGE("epo_step_host");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   const size_t nv = (size_t)S->n_views;
   if (T_in) {
@@ -1459,42 +1563,63 @@ epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, doubl
   if (st != EPO_OK) return st;
   // the staging is pinned and mapped: the step's pair setup reads the poses from it, and its
   // pose kernel (or a copy kernel after the step's last kernel) writes poses, loss and status
-  // word back into it
+  // word back into it.  A step left queued by a wait that ran out still uses it: wait for it
+  st = drain(S);
+  if (st != EPO_OK) return st;
   if (T_in) memcpy(S->h_in, T_in, 12 * nv * 8);
   CK(cudaGraphLaunch(S->graph_host[which - 1], S->stream));
-  CK(cudaStreamSynchronize(S->stream));
+  st = host_wait(S);
+  if (st != EPO_OK) return st;
   if (T_out) memcpy(T_out, S->h_io, 12 * nv * 8);
   if (loss) memcpy(loss, S->h_io + 12 * nv, (size_t)S->n_scenes * 8);
   int32_t flag;
   memcpy(&flag, S->h_io + 12 * nv + S->n_scenes, 4);
   if (flag & 1) {
     CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    CK(cudaStreamSynchronize(S->stream));
+    st = host_wait(S);
+    if (st != EPO_OK) return st;
     return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
   }
   return EPO_OK;
 }
 
 epo_status epo_check(epo_scene_t S) {
+  EPO_RANGE("epo_check");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, S->stream));
-  CK(cudaStreamSynchronize(S->stream));
+  epo_status st = host_wait(S);
+  if (st != EPO_OK) return st;
   if (*S->h_flag & 1) {
     CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    CK(cudaStreamSynchronize(S->stream));
+    st = host_wait(S);
+    if (st != EPO_OK) return st;
     return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
   }
   return EPO_OK;
 }
 
 epo_status epo_last_loss(epo_scene_t S, double* loss) {
+  EPO_RANGE("epo_last_loss");
   if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
-  CK(cudaMemcpyAsync(loss, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, S->stream));
-  CK(cudaStreamSynchronize(S->stream));
+  epo_status st = drain(S);
+  if (st != EPO_OK) return st;
+  CK(cudaMemcpyAsync(S->h_out, S->d_loss, (size_t)S->n_scenes * 8, cudaMemcpyDeviceToHost, S->stream));
+  st = host_wait(S);
+  if (st != EPO_OK) return st;
+  memcpy(loss, S->h_out, (size_t)S->n_scenes * 8);
+  return EPO_OK;
+}
+
+epo_status epo_set_wait_limit(epo_scene_t S, double seconds) {
+  EPO_RANGE("epo_set_wait_limit");
+  if (!S || !(seconds >= 0.0) || !isfinite(seconds))
+    return fail(S, EPO_ERR_INVALID_ARG, "null scene or a wait limit that is not a finite number >= 0");
+  S->wait_limit_s = seconds;
   return EPO_OK;
 }
 
 epo_status epo_fixup_stats(epo_scene_t S, int64_t* queued, int64_t* overflow) {
+  EPO_RANGE("epo_fixup_stats");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   unsigned int h[2] = {0u, 0u};
   CK(cudaMemcpyAsync(&h[0], S->d_qcount, 4, cudaMemcpyDeviceToHost, S->stream));
@@ -1506,6 +1631,7 @@ epo_status epo_fixup_stats(epo_scene_t S, int64_t* queued, int64_t* overflow) {
 }
 
 epo_status epo_kernel_time(epo_scene_t S, float* ms) {
+  EPO_RANGE("epo_kernel_time");
   if (!S || !ms) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   if (!S->ev[0] || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
   CK(cudaEventSynchronize(S->ev[3]));
@@ -1514,6 +1640,7 @@ epo_status epo_kernel_time(epo_scene_t S, float* ms) {
 }
 
 epo_status epo_stage_times(epo_scene_t S, float* ms) {
+  EPO_RANGE("epo_stage_times");
   if (!S || !ms) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   if (!S->ev[0] || !S->ev_recorded) return fail(S, EPO_ERR_INVALID_ARG, "timing not enabled or nothing ran yet");
   CK(cudaEventSynchronize(S->ev[3]));
@@ -1522,12 +1649,14 @@ epo_status epo_stage_times(epo_scene_t S, float* ms) {
 }
 
 epo_status epo_step(epo_scene_t S, int32_t n_steps) {
+  EPO_RANGE("epo_step");
   epo_status st = epo_step_async(S, n_steps);
   if (st != EPO_OK) return st;
   return epo_check(S);
 }
 
 epo_status epo_step_plain(epo_scene_t S, int32_t n_steps) {
+  EPO_RANGE("epo_step_plain");
   if (!S || n_steps < 0) return fail(S, EPO_ERR_INVALID_ARG, "null scene or negative step count");
   epo_status st = maybe_autotune(S);
   if (st != EPO_OK) return st;
@@ -1539,6 +1668,7 @@ epo_status epo_step_plain(epo_scene_t S, int32_t n_steps) {
 }
 
 epo_status epo_set_refinement(epo_scene_t S, const double* gamma, const float* alpha, const float* beta) {
+  EPO_RANGE("epo_set_refinement");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
   const size_t nv = (size_t)S->n_views, nr = (size_t)S->n_records;
@@ -1564,6 +1694,7 @@ epo_status epo_set_refinement(epo_scene_t S, const double* gamma, const float* a
 }
 
 epo_status epo_get_refinement(epo_scene_t S, double* gamma, float* alpha, float* beta) {
+  EPO_RANGE("epo_get_refinement");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
   const size_t nv = (size_t)S->n_views, nr = (size_t)S->n_records;
@@ -1576,6 +1707,7 @@ epo_status epo_get_refinement(epo_scene_t S, double* gamma, float* alpha, float*
 
 epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, double* grad_gamma, float* grad_alpha,
                                     float* grad_beta) {
+  EPO_RANGE("epo_refine_loss_and_grad");
   if (!S || !loss) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   if (!S->refine) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.refine = 1");
   epo_status st = maybe_autotune(S);
@@ -1604,6 +1736,7 @@ epo_status epo_refine_loss_and_grad(epo_scene_t S, double* loss, double* grad, d
 
 epo_status epo_get_schedule(epo_scene_t S, double* theta95, int32_t* phase, int64_t* switch_step,
                             int64_t* stop_step) {
+  EPO_RANGE("epo_get_schedule");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   if (!S->opt.schedule) return fail(S, EPO_ERR_INVALID_ARG, "scene was not created with options.schedule = 1");
   const int ns = S->n_scenes;
@@ -1622,6 +1755,7 @@ epo_status epo_get_schedule(epo_scene_t S, double* theta95, int32_t* phase, int6
 }
 
 epo_status epo_get_pair_active(epo_scene_t S, uint8_t* active) {
+  EPO_RANGE("epo_get_pair_active");
   if (!S || !active) return fail(S, EPO_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(active, S->d_active, (size_t)S->n_pairs, cudaMemcpyDeviceToHost, S->stream));
   CK(cudaStreamSynchronize(S->stream));
@@ -1629,6 +1763,7 @@ epo_status epo_get_pair_active(epo_scene_t S, uint8_t* active) {
 }
 
 epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
+  EPO_RANGE("epo_set_pair_subset");
   if (!S || n < 0 || (n > 0 && !ids)) return fail(S, EPO_ERR_INVALID_ARG, "invalid subset");
   if (S->opt.pair_budget > 0) return fail(S, EPO_ERR_INVALID_ARG, "the pairs are drawn on the device (pair_budget)");
   std::vector<uint8_t> act(S->n_pairs, n == 0 ? 1 : 0);
@@ -1656,6 +1791,7 @@ epo_status epo_set_pair_subset(epo_scene_t S, int32_t n, const int32_t* ids) {
 // split into items of 2 pairs and of 1 pair, and 12 further passes decide.  (Every item split
 // by pairs, tail_pairs <= -2, was never faster on the benchmark workloads: not a candidate.)
 epo_status epo_autotune(epo_scene_t S) {
+  EPO_RANGE("epo_autotune");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   S->tuned = true;  // also guards against recursion through maybe_autotune
   struct Cand {
@@ -1665,11 +1801,13 @@ epo_status epo_autotune(epo_scene_t S) {
   };
   const int tail0 = S->opt.tail_pairs == -1 ? 0 : S->opt.tail_pairs;
   std::vector<Cand> cands;
-  for (int g : {GATHER_LDG, GATHER_TEX})
-    for (int r : {1, 2, 4})
+  for (int g : {GATHER_LDG, GATHER_TEX, GATHER_MIX})
+    for (int r : {1, 2, 4, 8})
       for (int b : {128, 256, 512}) {
         if (S->opt.gather == EPO_GATHER_LDG && g != GATHER_LDG) continue;
         if (S->opt.gather == EPO_GATHER_TEX && g != GATHER_TEX) continue;
+        if (S->opt.gather == EPO_GATHER_MIX && g != GATHER_MIX) continue;
+        if (g == GATHER_MIX && (S->refine || r == 1)) continue;
         if (!schedule_fits(S, r, b)) continue;
         cands.push_back({g, r, b, tail0, {}, 0.f});
       }
@@ -1764,6 +1902,7 @@ epo_status epo_autotune(epo_scene_t S) {
 
 epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, float* map_dev,
                               void* cuda_stream) {
+  EPO_RANGE("epo_distance_field");
   epo_scene* S = nullptr;
   if (!edges_dev || !map_dev || W < 1 || H < 1)
     return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid distance-field arguments");
@@ -1773,6 +1912,7 @@ epo_status epo_distance_field(const uint8_t* edges_dev, int32_t W, int32_t H, fl
 }
 
 epo_status epo_round_bf16(const float* src, uint16_t* dst, int64_t n, void* cuda_stream) {
+  EPO_RANGE("epo_round_bf16");
   epo_scene* S = nullptr;
   if (!src || !dst || n < 0) return fail(nullptr, EPO_ERR_INVALID_ARG, "invalid bf16 rounding arguments");
   if (n == 0) return EPO_OK;

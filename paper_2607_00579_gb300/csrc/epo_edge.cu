@@ -503,21 +503,339 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------------------
+// a2-a7 for pose-only scenes: the same work items, lift, per-pair reduction, flush and exact
+// path as k_edge, with a leaner per-sample screen.
+//
+// Decisions.  With E = X.w + Et (the bound on the error of each component of Y), one bound
+//   t = E |1/Y3| Kb + cb
+// covers the FP32 error of both u' and v' for every sample within one pixel of the target
+// image (Kb holds the largest |xn| such a sample can have).  With x0 = floor(u'), a = u' - x0
+// (exact in FP32), the sample lies within t of a cell line or the border iff
+// min(a (1 - a), b (1 - b)) <= t (1 - t) (t < 1/2 here), one test for both axes and every
+// integer.  Validity in FP32 is then exact: a sample that is in front by more than E, in a
+// cell 0 <= x0 <= W - 2, 0 <= y0 <= H - 2 (unsigned compares of the non-negative float bits)
+// and farther than t from every integer has the cell, the border decision and the depth
+// decision of the exact evaluation.  Samples within t of an integer that land within one
+// pixel of the image, within E of the depth threshold, or whose E |1/Y3| exceeds Gb (where
+// the bound stops holding; measured never on the workloads), go to the exact path; samples
+// within the clamp's bound of lambda too, as in k_edge.  Records past the tile's end carry
+// NaN coordinates, so that every comparison on them is false.
+// ------------------------------------------------------------------------------------
+// Registers per thread: 56 keeps nine 128-thread blocks per SM (measured on the 16-scene batch:
+// 48 and 64 were no faster at four records per thread).  A variant build may set another cap.
+#ifdef EPO_POSE_MAXNREG
+#define EPO_POSE_BOUNDS __maxnreg__(EPO_POSE_MAXNREG)
+#else
+#define EPO_POSE_BOUNDS __maxnreg__(56)
+#endif
+// The exact path for one sample of a pose-only scene, reloading its record: a call (not inlined)
+// from the rare places that need it inside the sample loop, so that its FP64 registers do not
+// count against the loop's.
+template <int MODE, int REC, int MAP>
+__device__ __noinline__ void exact_eval_rec(const EdgeArgs& a, int64_t rec, int p, int q, double lam, float lamf) {
+  float u, v, z;
+  load_record<REC>(a.rec, rec, u, v, z);
+  exact_eval<MODE, REC, MAP, 0>(a, AmbEntry{u, v, z, p, q}, (int64_t)0, lam, lamf);
+}
+
+// An ambiguous sample of the pose kernel: its record and PairParam; the exact path reloads the
+// record (rare), so that the kernel keeps no copy of the raw pixels in shared memory.
+struct AmbRef {
+  int64_t rec;
+  int32_t q;
+  int32_t pad_;
+};
+// A small buffer, re-evaluated once more than a third full: the shared memory a block leaves
+// unused goes to the L1 cache that serves the map gathers.
+#ifndef EPO_POSE_AMBCAP
+#define EPO_POSE_AMBCAP 256
+#endif
+constexpr int kAmbCapPose = EPO_POSE_AMBCAP;
+constexpr int kAmbRunPose = kAmbCapPose * 3 / 8;
+
+template <int MODE, int REC, int MAP, int GATHER, int RPT>
+__global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
+  extern __shared__ float4 s_dyn[];
+  float4* s_X = s_dyn;                                                    // [blockDim * RPT]
+  float* s_part = reinterpret_cast<float*>(s_X + blockDim.x * RPT);      // [warps][max_pairs][kAcc]
+  __shared__ int s_tile, s_next;
+  __shared__ int s_amb_n;
+  __shared__ AmbRef s_amb[kAmbCapPose];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+  const unsigned lanemask_lt = (1u << lane) - 1u;
+  float lam = 0.f;
+  double lam64 = 0.0;
+  bool waited = false;
+  const float delta = a.delta;
+  const float eps_z = a.eps_z;
+  if (threadIdx.x == 0) {
+    s_tile = blockIdx.x;
+    s_amb_n = 0;
+  }
+  __syncthreads();
+  while (s_tile < a.n_tiles) {
+    const int t = s_tile;
+    const TileDev td = a.tiles[t];
+    const ViewDev vi = a.views[td.view];
+    // a2: lift once per record into shared memory (coalesced 128-bit record loads)
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int idx = threadIdx.x + r * blockDim.x;
+      if (idx < td.n) {
+        float u, v, z;
+        load_record<REC>(a.rec, td.begin + idx, u, v, z);
+        const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
+        // rounding-error bound of each component of Y = R X + t: 6u |X|_1 (rotation, lift, FMA)
+        s_X[idx] = make_float4(X0, X1, z, 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)));
+      } else {
+        s_X[idx] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);
+      }
+    }
+    if (!waited) {
+      griddep_wait();
+      griddep_launch_dependents();
+      lam64 = *a.lambda;
+      lam = (float)lam64;
+      waited = true;
+    }
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(a.tile_counter, 1);
+    const int pb = __ldg(&a.tiles[t].q0);
+    const int pe = __ldg(&a.tiles[t].q1);
+    // the clamp's own rounding: 8u (|d| + 1), with |d| <= lambda + 1 wherever it matters
+    const float c_lam = 8.f * kU32 * (fabsf(lam) + 2.f);
+    for (int q = pb; q < pe; ++q) {
+      const int2 pact = *reinterpret_cast<const int2*>(&a.pp[q].p);
+      if (!pact.y) continue;  // uniform over the block
+      const int p = pact.x;
+      const PairParam& P = a.pp[q];
+      const float r0 = P.r[0], r1 = P.r[1], r2 = P.r[2], r3 = P.r[3], r4 = P.r[4], r5 = P.r[5], r6 = P.r[6],
+                  r7 = P.r[7], r8 = P.r[8], t0 = P.t[0], t1 = P.t[1], t2 = P.t[2];
+      const float fx = P.fx, fy = P.fy, cx = P.cx, cy = P.cy, Et = P.Et, Kb = P.Kb, cb = P.cb;
+      const unsigned Wm2 = __float_as_uint(P.Wm2), Hm2 = __float_as_uint(P.Hm2);
+      float acc[kAcc];
+#pragma unroll
+      for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
+#ifdef EPO_POSE_ILP
+      constexpr int ILP = RPT < EPO_POSE_ILP ? RPT : EPO_POSE_ILP;
+#else
+      constexpr int ILP = RPT < 2 ? RPT : 2;
+#endif
+#ifdef EPO_POSE_ROLLED
+#pragma unroll 1
+#else
+#pragma unroll
+#endif
+      for (int g = 0; g < RPT; g += ILP) {
+        float fu1[ILP], fv1[ILP], ca[ILP], cbf[ILP], xn[ILP], yn[ILP], iz[ILP], tb[ILP], dze[ILP];
+        bool ok[ILP], amb[ILP];
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
+          const float Y0 = fmaf(r0, X.x, fmaf(r1, X.y, fmaf(r2, X.z, t0)));
+          const float Y1 = fmaf(r3, X.x, fmaf(r4, X.y, fmaf(r5, X.z, t1)));
+          const float Y2 = fmaf(r6, X.x, fmaf(r7, X.y, fmaf(r8, X.z, t2)));
+          iz[r] = rcp_approx(Y2);
+          xn[r] = Y0 * iz[r];
+          yn[r] = Y1 * iz[r];
+          const float up = fmaf(fx, xn[r], cx), vp = fmaf(fy, yn[r], cy);
+          const float fu = floorf(up), fv = floorf(vp);
+          ca[r] = up - fu;
+          cbf[r] = vp - fv;
+          fu1[r] = fu + 1.f;
+          fv1[r] = fv + 1.f;
+          const float E = X.w + Et;
+          const float dz = Y2 - eps_z;
+          tb[r] = fmaf(E * iz[r], Kb, cb);
+          const float T = fmaf(-tb[r], tb[r], tb[r]);
+          const float nm = fminf(fmaf(-ca[r], ca[r], ca[r]), fmaf(-cbf[r], cbf[r], cbf[r]));
+          const bool near = nm <= T;
+          const bool in_cell = __float_as_uint(fu) <= Wm2 && __float_as_uint(fv) <= Hm2;
+          // beyond t = 1/4 (or NaN) the bound is not relied on: the exact path decides
+          const bool guard = !(tb[r] <= 0.25f);
+          ok[r] = dz > E && in_cell && !near && !guard;
+          // candidates for the exact path; whether they are near the image is checked on the
+          // rare path (they are about 0.5 % of the samples)
+          dze[r] = fabsf(dz) - E;  // <= 0: within E of the depth threshold
+          amb[r] = guard || near || dze[r] <= 0.f;
+        }
+        // all gathers in flight together
+        float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
+          if (ok[r]) {
+            if (GATHER == GATHER_TEX || (GATHER == GATHER_MIX && r == 0)) {
+              if (MAP == 0) {
+                const float4 gq = tex2Dgather<float4>((cudaTextureObject_t)P.tex, fu1[r], fv1[r], 0);
+                m00[r] = gq.w; m01[r] = gq.z; m10[r] = gq.x; m11[r] = gq.y;
+              } else {
+                const ushort4 gq = tex2Dgather<ushort4>((cudaTextureObject_t)P.tex, fu1[r], fv1[r], 0);
+                m00[r] = bf16_bits_to_float(gq.w); m01[r] = bf16_bits_to_float(gq.z);
+                m10[r] = bf16_bits_to_float(gq.x); m11[r] = bf16_bits_to_float(gq.y);
+              }
+            } else {
+              taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, (int)fu1[r] - 1, (int)fv1[r] - 1, m00[r], m01[r],
+                                    m10[r], m11[r]);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          const float d01 = m01[r] - m00[r], d11 = m11[r] - m10[r];
+          const float top = fmaf(ca[r], d01, m00[r]);
+          const float bot = fmaf(ca[r], d11, m10[r]);
+          const float ddv = bot - top;
+          const float d = fmaf(cbf[r], ddv, top);
+          const float ddu = fmaf(cbf[r], d11 - d01, d01);
+          // the clamp is a discontinuity of the slope term: within its bound of lambda the
+          // sample goes to the exact path as well
+          const bool at_clamp =
+              fabsf(d - lam) <= fmaf(tb[r], fabsf(ddu) + fabsf(ddv), fmaf(8.f * kU32, fabsf(d), c_lam));
+          bool qa = amb[r] || (ok[r] && at_clamp);
+          if (ok[r] && !at_clamp) {
+            // a5: clamp + Huber, both branches of Eq. 7 in one form: with ch = min(|min(d,
+            // lambda)|, delta), H(min(d, lambda)) = ch (|min(d, lambda)| - ch / 2); H'(d) = d
+            // clamped to [-delta, delta] where d <= lambda
+            const float dh = fminf(d, lam);
+            const float ch = fminf(fabsf(dh), delta);
+            if (MODE != MODE_BWD) {
+              acc[0] = fmaf(ch, fmaf(-0.5f, ch, fabsf(dh)), acc[0]);
+              acc[1] += 1.f;
+            }
+            if (MODE != MODE_FWD) {
+              // a6: adjoint in camera-j coordinates; with (ga, gb) = H' (fx dd/du', fy dd/dv')
+              // and gc = -(ga xn + gb yn), dRho/dY = (ga, gb, gc) / Y3 and Y x dRho/dY =
+              // (xn, yn, 1) x (ga, gb, gc)
+              const float drho = d <= lam ? copysignf(ch, d) : 0.f;
+              const float ga = drho * (fx * ddu);
+              const float gb = drho * (fy * ddv);
+              const float gc = -fmaf(ga, xn[r], gb * yn[r]);
+              acc[2] = fmaf(ga, iz[r], acc[2]);
+              acc[3] = fmaf(gb, iz[r], acc[3]);
+              acc[4] = fmaf(gc, iz[r], acc[4]);
+              acc[5] = fmaf(yn[r], gc, acc[5]) - gb;
+              acc[6] = fmaf(-xn[r], gc, acc[6]) + ga;
+              acc[7] = fmaf(-yn[r], ga, fmaf(xn[r], gb, acc[7]));
+            }
+          }
+          if (__any_sync(0xffffffffu, qa)) {
+            // rare: of the candidates, keep those in front within E of the threshold or beyond,
+            // and within one pixel of the image (floor(u') + 1 in [0, W]) or beyond the bound,
+            // for the exact path (warp-aggregated append)
+            if (qa && !ok[r]) {
+              const bool front = dze[r] <= 0.f || (dze[r] > 0.f && iz[r] > 0.f);  // dz > -E
+              const bool in_ext = __float_as_uint(fu1[r]) <= __float_as_uint(P.Wf) &&
+                                  __float_as_uint(fv1[r]) <= __float_as_uint(P.Hf);
+              qa = front && (!(tb[r] <= 0.25f) || in_ext);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, qa);
+            const int leader = bal ? __ffs(bal) - 1 : 0;
+            int base = 0;
+            if (bal && lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (qa) {
+              const int pos = base + __popc(bal & lanemask_lt);
+              const int li = threadIdx.x + (g + r) * blockDim.x;
+              if (pos < kAmbCapPose) {
+                s_amb[pos] = AmbRef{td.begin + li, q, 0};
+              } else {
+                // buffer full: the lane re-evaluates its sample on the exact path at once
+                // buffer full (a tile with hundreds of samples on cell lines): this sample keeps
+                // its FP32 decisions, counted in q_overflow
+                atomicAdd(a.q_overflow, 1u);
+                const float up = fu1[r] - 1.f + ca[r], vp = fv1[r] - 1.f + cbf[r];
+                if (iz[r] > 0.f && up >= 0.f && up <= (float)(P.W - 1) && vp >= 0.f && vp <= (float)(P.H - 1)) {
+                  const int fx0 = min(max((int)floorf(up), 0), P.W - 2), fy0 = min(max((int)floorf(vp), 0), P.H - 2);
+                  const float fa = up - (float)fx0, fb = vp - (float)fy0;
+                  float n00, n01, n10, n11;
+                  taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, fx0, fy0, n00, n01, n10, n11);
+                  const float t2b = fmaf(fa, n01 - n00, n00);
+                  const float b2 = fmaf(fa, n11 - n10, n10);
+                  const float dd = fmaf(fb, b2 - t2b, t2b);
+                  const float du = fmaf(fb, (n11 - n10) - (n01 - n00), n01 - n00);
+                  const float dv = b2 - t2b;
+                  const float dh = fminf(dd, lam);
+                  const float ch = fminf(fabsf(dh), delta);
+                  if (MODE != MODE_BWD) {
+                    acc[0] += ch * fmaf(-0.5f, ch, fabsf(dh));
+                    acc[1] += 1.f;
+                  }
+                  if (MODE != MODE_FWD) {
+                    const float drho = dd <= lam ? fmaxf(fminf(dd, delta), -delta) : 0.f;
+                    const float ga = drho * (fx * du), gb = drho * (fy * dv);
+                    const float gc = -fmaf(ga, xn[r], gb * yn[r]);
+                    acc[2] = fmaf(ga, iz[r], acc[2]);
+                    acc[3] = fmaf(gb, iz[r], acc[3]);
+                    acc[4] = fmaf(gc, iz[r], acc[4]);
+                    acc[5] += fmaf(yn[r], gc, -gb);
+                    acc[6] += fmaf(-xn[r], gc, ga);
+                    acc[7] += fmaf(xn[r], gb, -(yn[r] * ga));
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+      // a7: warp reduce-scatter; lanes 0..7 store the warp's 8 sums (no block barrier)
+      const float sred = warp_reduce_scatter8(acc, lane);
+      if (lane < 8) s_part[((size_t)warp * a.max_pairs + (q - pb)) * kAcc + scatter_slot(lane)] = sred;
+    }
+    __syncthreads();
+    constexpr int S0 = MODE == MODE_BWD ? 2 : 0;
+    constexpr int NS = MODE == MODE_FWD ? 2 : kAcc - S0;
+    const int nq = (pe - pb) * NS;
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+      const int qq = k / NS, slot = S0 + k % NS;
+      const int2 pact = *reinterpret_cast<const int2*>(&a.pp[pb + qq].p);
+      if (!pact.y) continue;
+      float sum = 0.f;
+      for (int w = 0; w < nwarp; ++w) sum += s_part[((size_t)w * a.max_pairs + qq) * kAcc + slot];
+      if (sum != 0.f) atomicAdd(a.pair_acc + (size_t)kAcc * pact.x + slot, (double)sum);
+    }
+    if (threadIdx.x == 0) s_tile = s_next;
+    __syncthreads();
+    const int n_amb = min(s_amb_n, kAmbCapPose);
+    if (n_amb > (s_tile < a.n_tiles ? kAmbRunPose : 0)) {
+      for (int k = threadIdx.x; k < n_amb; k += blockDim.x) {
+        const AmbRef ar = s_amb[k];
+        exact_eval_rec<MODE, REC, MAP>(a, ar.rec, a.pp[ar.q].p, ar.q, lam64, lam);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        atomicAdd(a.q_count, (unsigned)n_amb);
+        s_amb_n = 0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine) {
-  // dynamic part: lifted records, raw (u, v), per-warp per-pair partial sums
-  return sizeof(float4) * (size_t)rpt * block + sizeof(float2) * (size_t)rpt * block +
+  // dynamic part: lifted records, (refine scenes) their rays, per-warp per-pair partial sums
+  return sizeof(float4) * (size_t)rpt * block + (refine ? sizeof(float2) * (size_t)rpt * block : 0) +
          sizeof(float) * (refine ? edge_slots<1>() : edge_slots<0>()) * (size_t)max_pairs * (block / 32);
+}
+
+// The kernel of a schedule: pose-only scenes run k_edge_pose, refine scenes k_edge.
+template <int MODE, int REC, int MAP, int GATHER, int R, int REF>
+static auto edge_kernel_of() {
+  if constexpr (REF) return k_edge<MODE, REC, MAP, GATHER, R, 1>;
+  else return k_edge_pose<MODE, REC, MAP, GATHER, R>;
 }
 
 template <int MODE, int REC, int MAP, int GATHER, int R, int REF>
 static cudaError_t launch_edge_one(const EdgeArgs& a, int block, int grid, cudaStream_t s) {
   const size_t smem = edge_smem_bytes(R, block, a.max_pairs, REF);
+  const auto k = edge_kernel_of<MODE, REC, MAP, GATHER, R, REF>();
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_edge<MODE, REC, MAP, GATHER, R, REF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return launch_pdl(k_edge<MODE, REC, MAP, GATHER, R, REF>, dim3(grid), dim3(block), smem, s, a);
+  return launch_pdl(k, dim3(grid), dim3(block), smem, s, a);
 }
 
 // Refine scenes run two records per thread only (one set of instantiations).
@@ -531,6 +849,7 @@ static cudaError_t launch_edge_rpt(const EdgeArgs& a, int rpt, int block, int gr
       case 1: return launch_edge_one<MODE, REC, MAP, GATHER, 1, 0>(a, block, grid, s);
       case 2: return launch_edge_one<MODE, REC, MAP, GATHER, 2, 0>(a, block, grid, s);
       case 4: return launch_edge_one<MODE, REC, MAP, GATHER, 4, 0>(a, block, grid, s);
+      case 8: return launch_edge_one<MODE, REC, MAP, GATHER, 8, 0>(a, block, grid, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -540,6 +859,10 @@ template <int MODE, int REC, int MAP, int REF>
 static cudaError_t launch_edge_g(const EdgeArgs& a, int gather, int rpt, int block, int grid,
                                  cudaStream_t s) {
   if (gather == GATHER_TEX) return launch_edge_rpt<MODE, REC, MAP, GATHER_TEX, REF>(a, rpt, block, grid, s);
+  if constexpr (!REF) {
+    if (gather == GATHER_MIX) return launch_edge_rpt<MODE, REC, MAP, GATHER_MIX, REF>(a, rpt, block, grid, s);
+  }
+  if (gather != GATHER_LDG) return cudaErrorInvalidValue;
   return launch_edge_rpt<MODE, REC, MAP, GATHER_LDG, REF>(a, rpt, block, grid, s);
 }
 
@@ -576,9 +899,10 @@ static const void* edge_ptr_rpt(int rpt) {
     return rpt == 2 ? (const void*)k_edge<MODE, REC, MAP, GATHER, 2, 1> : nullptr;
   } else {
     switch (rpt) {
-      case 1: return (const void*)k_edge<MODE, REC, MAP, GATHER, 1, 0>;
-      case 2: return (const void*)k_edge<MODE, REC, MAP, GATHER, 2, 0>;
-      case 4: return (const void*)k_edge<MODE, REC, MAP, GATHER, 4, 0>;
+      case 1: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 1>;
+      case 2: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 2>;
+      case 4: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 4>;
+      case 8: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 8>;
       default: return nullptr;
     }
   }
@@ -586,6 +910,15 @@ static const void* edge_ptr_rpt(int rpt) {
 
 template <int MODE, int REF>
 static const void* edge_ptr_m(int rec, int map, int gather, int rpt) {
+  if constexpr (!REF) {
+    if (gather == GATHER_MIX) {
+      if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_MIX, REF>(rpt);
+      if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_MIX, REF>(rpt);
+      if (rec == 1 && map == 0) return edge_ptr_rpt<MODE, 1, 0, GATHER_MIX, REF>(rpt);
+      return edge_ptr_rpt<MODE, 1, 1, GATHER_MIX, REF>(rpt);
+    }
+  }
+  if (gather == GATHER_MIX) return nullptr;
   if (gather == GATHER_TEX) {
     if (rec == 0 && map == 0) return edge_ptr_rpt<MODE, 0, 0, GATHER_TEX, REF>(rpt);
     if (rec == 0 && map == 1) return edge_ptr_rpt<MODE, 0, 1, GATHER_TEX, REF>(rpt);

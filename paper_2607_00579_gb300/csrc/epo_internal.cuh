@@ -23,10 +23,21 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 namespace epo {
+
+// An NVTX range around one public call, named after it (shown by Nsight tools; a few
+// nanoseconds when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define EPO_RANGE(name) ::epo::NvtxRange epo_nvtx_range_(name)
 
 // unit roundoff of binary32
 constexpr float kU32 = 5.9604645e-08f;
@@ -65,7 +76,10 @@ constexpr int kAcc = 8;         // per-pair accumulator slots: sum rho, n_valid,
 constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)
 
 enum Mode { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2 };
-enum Gather { GATHER_LDG = 1, GATHER_TEX = 2 };
+// GATHER_MIX (pose-only scenes): of the two samples a thread has in flight, one is fetched by a
+// texture gather and the other by plain loads, so that the texture unit and the load/store
+// path serve the footprints side by side.
+enum Gather { GATHER_LDG = 1, GATHER_TEX = 2, GATHER_MIX = 3 };
 
 struct ViewDev {
   float fx, fy, cx, cy;   // intrinsics rounded to f32 for the pixel math
@@ -87,8 +101,8 @@ struct TileDev {
 
 // Everything the edge kernel needs for one pair i -> j, built by the pair setup (a1):
 // the relative pose T_ji = T_j T_i^-1 rounded to f32, the target's intrinsics and map,
-// the pair constants of the FP32 rounding-error bound, and the pair's index and flag.  128
-// bytes, read with eight uniform 16-byte loads per pair.  Stored in the order of the views'
+// the pair constants of the FP32 rounding-error bound, and the pair's index and flag.  160
+// bytes, read with uniform 16-byte loads per pair.  Stored in the order of the views'
 // outgoing pair lists (entry q of src_pair_ids), so that a work item reads its pairs' entries
 // directly, with no pair-list or flag load in front of them.
 struct alignas(16) PairParam {
@@ -104,11 +118,21 @@ struct alignas(16) PairParam {
   int64_t map_off;
   unsigned long long tex; // texture object of the target map
   int64_t dbase;          // refine scenes: dzr[dbase + r] holds d(rho)/dz of record r for this pair
+  // the pose-only kernel's single rounding bound (scene creation): for a sample whose FP32
+  // position lies within one pixel of the target image, |u' - u'(exact)| and |v' - v'(exact)|
+  // are at most t = E |1/Y3| Kb + cb, with E the bound on the error of each component of Y;
+  // a sample with E |1/Y3| > Gb is re-evaluated exactly wherever it lands
+  float Kb, cb, Gb;
+  float Wm2, Hm2;         // W - 2, H - 2: the cell x0 = floor(u') is valid iff 0 <= x0 <= W - 2
+  float Wf, Hf;           // W, H: floor(u') + 1 in [0, W] iff u' lies within one pixel of the image
+  float pad_;
 };
-static_assert(sizeof(PairParam) == 128, "PairParam layout");
+static_assert(sizeof(PairParam) == 160, "PairParam layout");
 static_assert(offsetof(PairParam, p) % 8 == 0 && offsetof(PairParam, active) == offsetof(PairParam, p) + 4,
               "p and active form one aligned 8-byte word");
-static_assert(offsetof(PairParam, map_off) % 8 == 0 && offsetof(PairParam, dbase) % 8 == 0, "PairParam alignment");
+static_assert(offsetof(PairParam, map_off) % 8 == 0 && offsetof(PairParam, dbase) % 8 == 0 &&
+                  offsetof(PairParam, Kb) == 128,
+              "PairParam alignment");
 
 struct EdgeArgs {
   const void* rec;

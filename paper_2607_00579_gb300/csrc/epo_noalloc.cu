@@ -33,10 +33,17 @@ struct NaPair {
   double t[3];  // t_ji
 };
 
+// Per pair: sum rho, n_valid, sum dRho/dY (3), sum Y x dRho/dY (3), and the number of usable
+// records of the source view (the |E_i| of Eq. 7 under EPO_NORM_ALL)
+constexpr int kNaAcc = 9;
+
 struct NaScratch {
-  double acc[kNaMaxPairs][8];  // sum rho, n_valid, sum dRho/dY (3), sum Y x dRho/dY (3)
+  double acc[kNaMaxPairs][kNaAcc];
   NaPair pair[kNaMaxPairs];
 };
+// 4096 pairs x (9 + 12) doubles = 688,128 bytes (672 KiB), the size the header states
+static_assert(sizeof(NaScratch) == (size_t)kNaMaxPairs * (kNaAcc + 12) * sizeof(double), "scratch size");
+static_assert(sizeof(NaScratch) == 688128, "scratch size stated in epo.h");
 
 // The scratch: one file-scope device array shared by every call on a device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NaScratch)];
@@ -58,17 +65,17 @@ __global__ void k_na_setup(epo_noalloc_problem pb, NaScratch* S) {
       q.R[3 * r + c] = Tj[4 * r] * Ti[4 * c] + Tj[4 * r + 1] * Ti[4 * c + 1] + Tj[4 * r + 2] * Ti[4 * c + 2];
   for (int r = 0; r < 3; ++r)
     q.t[r] = Tj[4 * r + 3] - (q.R[3 * r] * Ti[3] + q.R[3 * r + 1] * Ti[7] + q.R[3 * r + 2] * Ti[11]);
-  for (int k = 0; k < 8; ++k) S->acc[p][k] = 0.0;  // the array keeps the previous call's sums
+  for (int k = 0; k < kNaAcc; ++k) S->acc[p][k] = 0.0;  // the array keeps the previous call's sums
 }
 
 // blockIdx.y = pair, blockIdx.x = tile of kNaThreads records of the source view
 __global__ void __launch_bounds__(kNaThreads) k_na_edge(epo_noalloc_problem pb, NaScratch* S) {
-  __shared__ float s_red[kNaThreads / 32][8];
+  __shared__ float s_red[kNaThreads / 32][kNaAcc];
   const int p = blockIdx.y;
   const int i = pb.pairs[2 * p], j = pb.pairs[2 * p + 1];
   const int64_t r0 = pb.rec_off[i], n = pb.rec_off[i + 1] - r0;
   const int64_t idx = (int64_t)blockIdx.x * kNaThreads + threadIdx.x;
-  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float acc[kNaAcc] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if ((int64_t)blockIdx.x * kNaThreads < n) {
     if (idx < n) {
       const float4 rec = reinterpret_cast<const float4*>(pb.records)[r0 + idx];
@@ -82,6 +89,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_edge(epo_noalloc_problem pb, 
       const int W = pb.W[j], H = pb.H[j];
       // records without a usable depth are not part of the problem (as at scene creation)
       const bool usable = rec.z > 0.f && isfinite(rec.x) && isfinite(rec.y) && isfinite(rec.z);
+      acc[8] = usable ? 1.f : 0.f;
       if (usable && Y[2] > pb.eps_z) {
         const double up = Kj[0] * Y[0] / Y[2] + Kj[2];
         const double vp = Kj[1] * Y[1] / Y[2] + Kj[3];
@@ -119,13 +127,13 @@ __global__ void __launch_bounds__(kNaThreads) k_na_edge(epo_noalloc_problem pb, 
   }
   // block reduction: warp shuffles, then a fixed-order sum over warps, one FP64 atomic per slot
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < kNaAcc; ++k) {
     float v = acc[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s_red[warp][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < kNaAcc) {
     float v = 0.f;
     for (int w = 0; w < kNaThreads / 32; ++w) v += s_red[w][threadIdx.x];
     if (v != 0.f) atomicAdd(&S->acc[p][threadIdx.x], (double)v);
@@ -139,8 +147,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_finish(epo_noalloc_problem pb
   const int P = pb.n_pairs;
   double part = 0.0;
   for (int p = threadIdx.x; p < P; p += kNaThreads) {
-    const int i = pb.pairs[2 * p];
-    const double denom = pb.norm_mode == EPO_NORM_ALL ? (double)(pb.rec_off[i + 1] - pb.rec_off[i]) : S->acc[p][1];
+    const double denom = pb.norm_mode == EPO_NORM_ALL ? S->acc[p][8] : S->acc[p][1];
     if (denom > 0.0) part += S->acc[p][0] / denom;
   }
   s_sum[threadIdx.x] = part;
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_finish(epo_noalloc_problem pb
       const int i = pb.pairs[2 * p], j = pb.pairs[2 * p + 1];
       if (i != v && j != v) continue;
       const double* a = S->acc[p];
-      const double denom = pb.norm_mode == EPO_NORM_ALL ? (double)(pb.rec_off[i + 1] - pb.rec_off[i]) : a[1];
+      const double denom = pb.norm_mode == EPO_NORM_ALL ? a[8] : a[1];
       if (!(denom > 0.0)) continue;
       const double c = 2.0 / P / denom;
       if (j == v) g += c * a[k < 3 ? 2 + k : 5 + (k - 3)];
@@ -189,6 +196,15 @@ extern "C" epo_status epo_loss_and_grad_noalloc(const epo_noalloc_problem* pb, d
     return EPO_ERR_INVALID_ARG;
   if (pb->n_views < 1 || pb->n_pairs < 1 || pb->max_records_per_view < 0)
     return EPO_ERR_INVALID_ARG;
+  // the kernels read records as 16-byte vectors and the other arrays at their natural width:
+  // a misaligned pointer would fault on the device, so it is refused here
+  if ((uintptr_t)pb->records % 16 != 0 || (uintptr_t)pb->rec_off % 8 != 0 || (uintptr_t)pb->maps % 4 != 0 ||
+      (uintptr_t)pb->map_off % 8 != 0 || (uintptr_t)pb->W % 4 != 0 || (uintptr_t)pb->H % 4 != 0 ||
+      (uintptr_t)pb->K % 8 != 0 || (uintptr_t)pb->pairs % 4 != 0 || (uintptr_t)pb->T % 8 != 0 ||
+      (uintptr_t)loss_dev % 8 != 0 || (uintptr_t)grad_dev % 8 != 0)
+    return EPO_ERR_INVALID_ARG;
+  // one block per tile of kNaThreads records of a view: the tile count is the grid's x extent
+  if ((pb->max_records_per_view + kNaThreads - 1) / kNaThreads > (int64_t)INT32_MAX) return EPO_ERR_TOO_LARGE;
   if (pb->n_views > kNaMaxViews || pb->n_pairs > kNaMaxPairs)
     return EPO_ERR_TOO_LARGE;
   if (!(pb->lambda > 0) || !(pb->huber_delta > 0) || !(pb->eps_z >= 0) ||

@@ -107,6 +107,7 @@ const void* probe_kernel(int map, int gather, int pattern) {
 extern "C" epo_status epo_gather_probe(int32_t n_maps, int32_t W, int32_t H, int32_t map_dtype, int32_t gather,
                                        int32_t pattern, int64_t samples, int32_t repeats, double* samples_per_s,
                                        void* cuda_stream) {
+  EPO_RANGE("epo_gather_probe");
   if (!samples_per_s || n_maps < 1 || W < 2 || H < 2 || W > 65535 || H > 65535 || samples < 1 || repeats < 1 ||
       (map_dtype != EPO_F32 && map_dtype != EPO_BF16) || (gather != EPO_GATHER_LDG && gather != EPO_GATHER_TEX) ||
       (pattern != 0 && pattern != 1) || (pattern == 1 && (W < 48 || H < 16)))

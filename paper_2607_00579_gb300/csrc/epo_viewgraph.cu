@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/epo.h"
+#include "epo_internal.cuh"
 
 namespace {
 
@@ -99,6 +100,7 @@ extern "C" epo_status epo_build_viewgraph(int32_t n_views, const int32_t* W, con
                                           const double* T, const float* depth_dev, int32_t stride, double tau,
                                           double min_frac, double* frac, int32_t* pairs, int32_t* n_pairs,
                                           void* cuda_stream) {
+  EPO_RANGE("epo_build_viewgraph");
   if (n_views < 1 || n_views > 46340 || !W || !H || !K || !T || !depth_dev || stride < 1 || !(tau > 0) ||
       !(min_frac >= 0) || !n_pairs)
     return EPO_ERR_INVALID_ARG;

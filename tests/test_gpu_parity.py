@@ -92,9 +92,12 @@ def allowances(o, pairs, T, n_views, lam, delta):
 def check_against_oracle(loss_g, grad_g, o, pairs, T, lam=10.0, delta=1.0, stats=None, grad_scale=1.0,
                          slope_pairs=None, gref=0.0):
     """slope_pairs: boolean mask of the pairs whose per-pair slope sums are compared (default all).
-    gref: gradient scale of the problem (max ||g_i|| at its initial poses) when the poses are
-    further along an optimisation: the FP32 error is a fixed absolute amount set by the
-    per-sample terms, which stay O(1) while their sum, the gradient, shrinks near the optimum."""
+    gref: gradient scale of the problem, max ||g_i|| at a run's initial poses, for poses further
+    along an optimisation: the FP32 error is a fixed absolute
+    amount set by the per-sample terms (measured 4.7e-5 to 8.7e-5 along the 200-step 32-view
+    ring), which stay O(1) while their sum, the gradient, shrinks near the optimum (there up to
+    1.8e-4 of the current gradient).  The tolerance is 1e-4 of the larger of gref and the
+    current max ||g_i||."""
     allow_L, allow_g = allowances(o, pairs, T, len(grad_g), lam, delta)
     assert abs(loss_g - o["loss"]) <= LOSS_RTOL * abs(o["loss"]) + allow_L, (loss_g, o["loss"], allow_L)
     err = np.linalg.norm(np.asarray(grad_g) - o["grad"], axis=1)
@@ -116,8 +119,12 @@ def check_against_oracle(loss_g, grad_g, o, pairs, T, lam=10.0, delta=1.0, stats
 
 
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("gather", [epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX])
-@pytest.mark.parametrize("rpt,block", [(4, 256), (2, 128), (1, 512)])
+SCHEDULES = [(g, r, b) for g in (epo.EPO_GATHER_LDG, epo.EPO_GATHER_TEX) for r, b in ((4, 256), (2, 128), (1, 512))]
+SCHEDULES += [(epo.EPO_GATHER_MIX, 2, 128), (epo.EPO_GATHER_MIX, 4, 256), (epo.EPO_GATHER_LDG, 8, 128),
+              (epo.EPO_GATHER_TEX, 8, 64), (epo.EPO_GATHER_MIX, 8, 512)]
+
+
+@pytest.mark.parametrize("gather,rpt,block", SCHEDULES)
 def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
     sc, maps = ring8
     s = gpu_scene(sc, maps, gather=gather, records_per_thread=rpt, block_threads=block)
@@ -478,15 +485,14 @@ def test_autotune_keeps_results(ring8):
 @pytest.fixture(scope="module")
 def ring32():
     sc = synth.make_scene(synth.RING32_518x392)
-    e = [torch.from_numpy(x).cuda() for x in sc.edges]
-    maps = [epo.distance_field(x).cpu().numpy() for x in e]
-    return sc, maps
+    return sc, oracle_maps_f32(sc)
 
 
 def test_full_size_sampled_pairs_match_oracle(ring32):
     sc, maps = ring32
-    for v in (0, 7, 31):
-        assert np.array_equal(maps[v], oracle.edt(sc.edges[v]).astype(np.float32))
+    for v in (0, 7, 31):  # the GPU's distance transform gives the same maps
+        g = epo.distance_field(torch.from_numpy(sc.edges[v]).cuda()).cpu().numpy()
+        assert np.array_equal(g, maps[v])
     s = gpu_scene(sc, maps)
     s.set_poses(sc.T_init)
     loss, grad = s.loss_and_grad()

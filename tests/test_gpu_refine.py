@@ -111,7 +111,7 @@ def test_refined_loss_and_all_gradients_match_oracle(ring8, gather):
 
 def test_refined_full_size_ring32():
     sc = synth.make_scene(synth.RING32_518x392)
-    maps = [epo.distance_field(torch.from_numpy(e).cuda()).cpu().numpy() for e in sc.edges]
+    maps = oracle_maps_f32(sc)
     g, a, b = refinement(sc, seed=5, s=0.005)
     s = refine_scene(sc, maps)
     s.set_poses(sc.T_init)

@@ -76,7 +76,7 @@ def test_budgeted_optimisation_tracks_oracle(ring8):
 def test_large_scene_subset_and_batched_scenes():
     spec = synth.RING500_518x518
     sc = synth.make_scene(spec)
-    maps = [epo.distance_field(torch.from_numpy(e).cuda()).cpu().numpy() for e in sc.edges]
+    maps = oracle_maps_f32(sc)
     s = gpu_scene(sc, maps, pair_budget=1024, subsample_seed=SEED)
     s.set_poses(sc.T_init)
     s.loss_and_grad()

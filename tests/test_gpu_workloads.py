@@ -39,12 +39,6 @@ def apply_left(T, v, xi):
     return T
 
 
-def gpu_maps(sc):
-    """Distance fields of every view from the GPU distance-transform kernel (exact, checked
-    against the oracle's EDT by the parity tests)."""
-    return [epo.distance_field(torch.from_numpy(e).cuda()).cpu().numpy() for e in sc.edges]
-
-
 @pytest.fixture(scope="module")
 def ring32():
     sc = synth.make_scene(synth.RING32_518x392)
@@ -153,9 +147,10 @@ def test_ring32_200_steps_track_oracle(ring32):
 # ---------------------------------------------------------------------------------------------
 def test_walk200_loss_grad_matches_oracle_and_adjoint_memory():
     sc = synth.make_scene(synth.WALK200_518x392)
-    maps = gpu_maps(sc)
-    for v in (0, 99, 199):
-        assert np.array_equal(maps[v], oracle.edt(sc.edges[v]).astype(np.float32))
+    maps = oracle_maps_f32(sc)
+    for v in (0, 99, 199):  # the GPU's distance transform gives the same maps
+        g = epo.distance_field(torch.from_numpy(sc.edges[v]).cuda()).cpu().numpy()
+        assert np.array_equal(g, maps[v])
     s = gpu_scene(sc, maps)
     s.set_poses(sc.T_init)
     evals = s.info().evals_per_step
@@ -188,7 +183,7 @@ def test_walk200_loss_grad_matches_oracle_and_adjoint_memory():
 def test_uneven_batch_graph_step_equals_plain_per_scene_steps():
     specs = synth.batch64_uneven_specs()[:6]
     scenes = [synth.make_scene(sp) for sp in specs]
-    maps = [gpu_maps(sc) for sc in scenes]
+    maps = [oracle_maps_f32(sc) for sc in scenes]
     b = epo.Scene([scene_part(sc, m) for sc, m in zip(scenes, maps)])
     b.set_poses(np.concatenate([sc.T_init for sc in scenes]))
     lb, gb = b.loss_and_grad()
@@ -217,7 +212,7 @@ def test_uneven_batch_graph_step_equals_plain_per_scene_steps():
 @pytest.fixture(scope="module")
 def ring500():
     sc = synth.make_scene(synth.RING500_518x518)
-    return sc, gpu_maps(sc)
+    return sc, oracle_maps_f32(sc)
 
 
 def mixed_precision_scene(sc, maps, **kw):
@@ -254,9 +249,8 @@ def test_ring500_bf16_fp16_subset_parity_and_precision_cost(ring500):
     r = o_full.loss_grad(sc.T_init, lam=10.0)
     assert abs(loss[0] - r["loss"]) <= 1e-2 * r["loss"]
     assert grad_rel_err(grad, r["grad"]) <= 1e-2
-    # the optimisation: kernel parity along the GPU's trajectory, and the same final accuracy
-    # as the oracle on full-precision inputs
-    g0 = np.linalg.norm(o_same.loss_grad(sc.T_init, lam=10.0)["grad"], axis=1).max()
+    # the optimisation: kernel parity along the GPU's trajectory (against the current gradient),
+    # and the same final accuracy as the oracle on full-precision inputs
     step = 0
     for c in (50, 100):
         s.step(c - step)
@@ -264,7 +258,7 @@ def test_ring500_bf16_fp16_subset_parity_and_precision_cost(ring500):
         T = s.get_poses()
         loss, grad = s.loss_and_grad()
         check_against_oracle(loss[0], grad, o_same.loss_grad(T, lam=oracle.lambda_at(step)), sc.pairs, T,
-                             lam=oracle.lambda_at(step), gref=g0)
+                             lam=oracle.lambda_at(step))
     To, _, _, _ = o_full.optimize(sc.T_init, sc.fixed, 100, **kw)
     same_accuracy(s.get_poses(), To, sc)
 
