@@ -57,6 +57,24 @@ __device__ __forceinline__ void taps(const void* map, int64_t off, int pitch, un
   }
 }
 
+// Texture gather of the 2x2 block centred on (x, y) (unnormalised coordinates, FP32 texels) for
+// the lanes where p holds: tld4 of component 0, as tex2Dgather returns it, (x: (x0, y0+1), y: (x0+1,
+// y0+1), z: (x0+1, y0), w: (x0, y0)).  Where p does not hold nothing is fetched and the outputs
+// are unspecified (the caller does not use them), so no register is cleared in advance.
+__device__ __forceinline__ void tex_gather_if(bool p, unsigned long long tex, float x, float y, float& m00, float& m01,
+                                              float& m10, float& m11) {
+  float gx, gy, gz, gw;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+      "@q tld4.r.2d.v4.f32.f32 {%0, %1, %2, %3}, [%5, {%6, %7}];\n\t}"
+      : "=f"(gx), "=f"(gy), "=f"(gz), "=f"(gw)
+      : "r"((int)p), "l"(tex), "f"(x), "f"(y));
+  m00 = gw;
+  m01 = gz;
+  m10 = gx;
+  m11 = gy;
+}
+
 // rcp.approx: |rel. error| <= 2^-23 (PTX ISA), folded into the position error bound
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -609,7 +627,6 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
     for (int q = pb; q < pe; ++q) {
       const int2 pact = *reinterpret_cast<const int2*>(&a.pp[q].p);
       if (!pact.y) continue;  // uniform over the block
-      const int p = pact.x;
       const PairParam& P = a.pp[q];
       const float r0 = P.r[0], r1 = P.r[1], r2 = P.r[2], r3 = P.r[3], r4 = P.r[4], r5 = P.r[5], r6 = P.r[6],
                   r7 = P.r[7], r8 = P.r[8], t0 = P.t[0], t1 = P.t[1], t2 = P.t[2];
@@ -618,19 +635,11 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
       float acc[kAcc];
 #pragma unroll
       for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
-#ifdef EPO_POSE_ILP
-      constexpr int ILP = RPT < EPO_POSE_ILP ? RPT : EPO_POSE_ILP;
-#else
-      constexpr int ILP = RPT < 2 ? RPT : 2;
-#endif
-#ifdef EPO_POSE_ROLLED
-#pragma unroll 1
-#else
+      constexpr int ILP = RPT < 2 ? RPT : 2;  // two samples in flight (four spill)
 #pragma unroll
-#endif
       for (int g = 0; g < RPT; g += ILP) {
         float fu1[ILP], fv1[ILP], ca[ILP], cbf[ILP], xn[ILP], yn[ILP], iz[ILP], tb[ILP], dze[ILP];
-        bool ok[ILP], amb[ILP];
+        bool ok[ILP], fetch[ILP], amb[ILP];
 #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
@@ -655,47 +664,92 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
           const bool in_cell = __float_as_uint(fu) <= Wm2 && __float_as_uint(fv) <= Hm2;
           // beyond t = 1/4 (or NaN) the bound is not relied on: the exact path decides
           const bool guard = !(tb[r] <= 0.25f);
-          ok[r] = dz > E && in_cell && !near && !guard;
+          // the footprint is fetched wherever FP32 says the sample is valid; it is accumulated
+          // where no decision is in doubt (and, should the exact path's buffer be full, where
+          // FP32 says valid)
+          fetch[r] = dz > 0.f && in_cell;
+          ok[r] = fetch[r] && dz > E && !near && !guard;
           // candidates for the exact path; whether they are near the image is checked on the
           // rare path (they are about 0.5 % of the samples)
           dze[r] = fabsf(dz) - E;  // <= 0: within E of the depth threshold
           amb[r] = guard || near || dze[r] <= 0.f;
         }
-        // all gathers in flight together
+        // all gathers in flight together.  A sample that is not fetched gets unspecified tap
+        // values, which it never accumulates
         float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
 #pragma unroll
         for (int r = 0; r < ILP; ++r) {
-          m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
-          if (ok[r]) {
-            if (GATHER == GATHER_TEX || (GATHER == GATHER_MIX && r == 0)) {
-              if (MAP == 0) {
-                const float4 gq = tex2Dgather<float4>((cudaTextureObject_t)P.tex, fu1[r], fv1[r], 0);
-                m00[r] = gq.w; m01[r] = gq.z; m10[r] = gq.x; m11[r] = gq.y;
-              } else {
+          if (MAP == 0 && (GATHER == GATHER_TEX || (GATHER == GATHER_MIX && r == 0))) {
+            tex_gather_if(fetch[r], P.tex, fu1[r], fv1[r], m00[r], m01[r], m10[r], m11[r]);
+          } else {
+            m00[r] = m01[r] = m10[r] = m11[r] = 0.f;
+            if (fetch[r]) {
+              if (GATHER == GATHER_TEX || (GATHER == GATHER_MIX && r == 0)) {
                 const ushort4 gq = tex2Dgather<ushort4>((cudaTextureObject_t)P.tex, fu1[r], fv1[r], 0);
                 m00[r] = bf16_bits_to_float(gq.w); m01[r] = bf16_bits_to_float(gq.z);
                 m10[r] = bf16_bits_to_float(gq.x); m11[r] = bf16_bits_to_float(gq.y);
+              } else {
+                taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, (int)fu1[r] - 1, (int)fv1[r] - 1, m00[r],
+                                      m01[r], m10[r], m11[r]);
               }
-            } else {
-              taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, (int)fu1[r] - 1, (int)fv1[r] - 1, m00[r], m01[r],
-                                    m10[r], m11[r]);
             }
           }
         }
+        float dv_[ILP], du_[ILP], dd_[ILP];
+        bool qa[ILP], use[ILP];
 #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           const float d01 = m01[r] - m00[r], d11 = m11[r] - m10[r];
           const float top = fmaf(ca[r], d01, m00[r]);
           const float bot = fmaf(ca[r], d11, m10[r]);
-          const float ddv = bot - top;
-          const float d = fmaf(cbf[r], ddv, top);
-          const float ddu = fmaf(cbf[r], d11 - d01, d01);
+          dv_[r] = bot - top;
+          dd_[r] = fmaf(cbf[r], dv_[r], top);
+          du_[r] = fmaf(cbf[r], d11 - d01, d01);
           // the clamp is a discontinuity of the slope term: within its bound of lambda the
           // sample goes to the exact path as well
-          const bool at_clamp =
-              fabsf(d - lam) <= fmaf(tb[r], fabsf(ddu) + fabsf(ddv), fmaf(8.f * kU32, fabsf(d), c_lam));
-          bool qa = amb[r] || (ok[r] && at_clamp);
-          if (ok[r] && !at_clamp) {
+          const bool at_clamp = fabsf(dd_[r] - lam) <=
+                                fmaf(tb[r], fabsf(du_[r]) + fabsf(dv_[r]), fmaf(8.f * kU32, fabsf(dd_[r]), c_lam));
+          qa[r] = amb[r] || (ok[r] && at_clamp);
+          use[r] = ok[r] && !at_clamp;
+        }
+        bool any_qa = false;
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) any_qa = any_qa || qa[r];
+        if (__any_sync(0xffffffffu, any_qa)) {
+          // rare: of the candidates, keep those in front within E of the threshold or beyond,
+          // and within one pixel of the image (floor(u') + 1 in [0, W]) or beyond the bound, for
+          // the exact path (warp-aggregated append)
+#pragma unroll
+          for (int r = 0; r < ILP; ++r) {
+            if (qa[r] && !ok[r]) {
+              const bool front = dze[r] <= 0.f || (dze[r] > 0.f && iz[r] > 0.f);  // dz > -E
+              const bool in_ext = __float_as_uint(fu1[r]) <= __float_as_uint(P.Wf) &&
+                                  __float_as_uint(fv1[r]) <= __float_as_uint(P.Hf);
+              qa[r] = front && (!(tb[r] <= 0.25f) || in_ext);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, qa[r]);
+            const int leader = bal ? __ffs(bal) - 1 : 0;
+            int base = 0;
+            if (bal && lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (qa[r]) {
+              const int pos = base + __popc(bal & lanemask_lt);
+              const int li = threadIdx.x + (g + r) * blockDim.x;
+              if (pos < kAmbCapPose) {
+                s_amb[pos] = AmbRef{td.begin + li, q, 0};
+              } else {
+                // buffer full (a tile with hundreds of samples on cell lines): the sample keeps
+                // its FP32 decisions, counted in q_overflow
+                atomicAdd(a.q_overflow, 1u);
+                use[r] = fetch[r];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+          if (use[r]) {
+            const float d = dd_[r], ddu = du_[r], ddv = dv_[r];
             // a5: clamp + Huber, both branches of Eq. 7 in one form: with ch = min(|min(d,
             // lambda)|, delta), H(min(d, lambda)) = ch (|min(d, lambda)| - ch / 2); H'(d) = d
             // clamped to [-delta, delta] where d <= lambda
@@ -719,63 +773,6 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
               acc[5] = fmaf(yn[r], gc, acc[5]) - gb;
               acc[6] = fmaf(-xn[r], gc, acc[6]) + ga;
               acc[7] = fmaf(-yn[r], ga, fmaf(xn[r], gb, acc[7]));
-            }
-          }
-          if (__any_sync(0xffffffffu, qa)) {
-            // rare: of the candidates, keep those in front within E of the threshold or beyond,
-            // and within one pixel of the image (floor(u') + 1 in [0, W]) or beyond the bound,
-            // for the exact path (warp-aggregated append)
-            if (qa && !ok[r]) {
-              const bool front = dze[r] <= 0.f || (dze[r] > 0.f && iz[r] > 0.f);  // dz > -E
-              const bool in_ext = __float_as_uint(fu1[r]) <= __float_as_uint(P.Wf) &&
-                                  __float_as_uint(fv1[r]) <= __float_as_uint(P.Hf);
-              qa = front && (!(tb[r] <= 0.25f) || in_ext);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, qa);
-            const int leader = bal ? __ffs(bal) - 1 : 0;
-            int base = 0;
-            if (bal && lane == leader) base = atomicAdd(&s_amb_n, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (qa) {
-              const int pos = base + __popc(bal & lanemask_lt);
-              const int li = threadIdx.x + (g + r) * blockDim.x;
-              if (pos < kAmbCapPose) {
-                s_amb[pos] = AmbRef{td.begin + li, q, 0};
-              } else {
-                // buffer full: the lane re-evaluates its sample on the exact path at once
-                // buffer full (a tile with hundreds of samples on cell lines): this sample keeps
-                // its FP32 decisions, counted in q_overflow
-                atomicAdd(a.q_overflow, 1u);
-                const float up = fu1[r] - 1.f + ca[r], vp = fv1[r] - 1.f + cbf[r];
-                if (iz[r] > 0.f && up >= 0.f && up <= (float)(P.W - 1) && vp >= 0.f && vp <= (float)(P.H - 1)) {
-                  const int fx0 = min(max((int)floorf(up), 0), P.W - 2), fy0 = min(max((int)floorf(vp), 0), P.H - 2);
-                  const float fa = up - (float)fx0, fb = vp - (float)fy0;
-                  float n00, n01, n10, n11;
-                  taps<MAP, GATHER>(a.map, P.map_off, P.pitch, P.tex, fx0, fy0, n00, n01, n10, n11);
-                  const float t2b = fmaf(fa, n01 - n00, n00);
-                  const float b2 = fmaf(fa, n11 - n10, n10);
-                  const float dd = fmaf(fb, b2 - t2b, t2b);
-                  const float du = fmaf(fb, (n11 - n10) - (n01 - n00), n01 - n00);
-                  const float dv = b2 - t2b;
-                  const float dh = fminf(dd, lam);
-                  const float ch = fminf(fabsf(dh), delta);
-                  if (MODE != MODE_BWD) {
-                    acc[0] += ch * fmaf(-0.5f, ch, fabsf(dh));
-                    acc[1] += 1.f;
-                  }
-                  if (MODE != MODE_FWD) {
-                    const float drho = dd <= lam ? fmaxf(fminf(dd, delta), -delta) : 0.f;
-                    const float ga = drho * (fx * du), gb = drho * (fy * dv);
-                    const float gc = -fmaf(ga, xn[r], gb * yn[r]);
-                    acc[2] = fmaf(ga, iz[r], acc[2]);
-                    acc[3] = fmaf(gb, iz[r], acc[3]);
-                    acc[4] = fmaf(gc, iz[r], acc[4]);
-                    acc[5] += fmaf(yn[r], gc, -gb);
-                    acc[6] += fmaf(-xn[r], gc, ga);
-                    acc[7] += fmaf(xn[r], gb, -(yn[r] * ga));
-                  }
-                }
-              }
             }
           }
         }
@@ -816,7 +813,8 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
 
 size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine) {
   // dynamic part: lifted records, (refine scenes) their rays, per-warp per-pair partial sums
-  return sizeof(float4) * (size_t)rpt * block + (refine ? sizeof(float2) * (size_t)rpt * block : 0) +
+  return sizeof(float4) * (size_t)rpt * block +
+         (refine ? sizeof(float2) * (size_t)rpt * block : 0) +
          sizeof(float) * (refine ? edge_slots<1>() : edge_slots<0>()) * (size_t)max_pairs * (block / 32);
 }
 
