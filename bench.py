@@ -486,6 +486,9 @@ def run_ours(args):
     roof = roofline_line(wl, info, evals, kern_avg, gather_roof, traffic, peak, peak_src)
     st_avg = np.mean(np.array(stages), axis=0)
     queued, overflow = epo._binding.epo_fixup_stats(st_.handle)
+    # samples of the last evaluated step that were valid (in front, inside the target image):
+    # the footprints the gathers had to serve
+    valid_evals = int(round(float(st_.pair_stats()[:, 1].sum())))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f16 gathers, f32" if wl.mixed else "f32",
@@ -502,7 +505,7 @@ def run_ours(args):
             "gather_roofline": gather_roof,
             "stages_ms": {"pair_setup": float(st_avg[0]), "edge_with_exact_path": float(st_avg[1]),
                           "poses": float(st_avg[2])},
-            "exact_fixup_samples": queued, "exact_fixup_overflow": overflow,
+            "exact_fixup_samples": queued, "exact_fixup_overflow": overflow, "valid_evals": valid_evals,
             "wall_ms_per_step": 1e3 * t_wall / args.steps}
     del st_
     if args.no_legs:

@@ -55,7 +55,10 @@ typedef enum {
   EPO_ERR_OOM = 3,         /* device allocation failed */
   EPO_ERR_NUMERIC = 4,     /* non-finite loss or gradient; the pose update was refused */
   EPO_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
-  EPO_ERR_INTERNAL = 6,    /* a device-side consistency check failed */
+  EPO_ERR_INTERNAL = 6,    /* a device-side consistency check failed: in builds with
+                              EPO_DEBUG_BOUNDS, a gather cell outside its map (the sample is
+                              skipped, the poses are not updated; the message names the
+                              first offending pair and cell) */
   EPO_ERR_TOO_LARGE = 7    /* the problem exceeds a fixed capacity (epo_loss_and_grad_noalloc) */
 } epo_status;
 

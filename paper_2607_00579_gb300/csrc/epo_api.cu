@@ -107,6 +107,7 @@ struct epo_scene {
   int max_pairs = 1;
   int64_t* d_step = nullptr;
   int32_t* d_flag = nullptr;
+  int32_t* d_dbg = nullptr;   // the first out-of-map gather of a debug build (pair, x0, y0; pair -1 = none)
   unsigned long long* d_done = nullptr;
   // loss chunks: 32 consecutive pairs of one scene per pose-kernel block
   int32_t n_loss_chunks = 0;
@@ -195,6 +196,31 @@ epo_status cuda_fail(epo_scene* s, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                             \
     if (e_ != cudaSuccess) return cuda_fail(S, e_, #call); \
   } while (0)
+
+epo_status host_wait(epo_scene* S);
+
+// The status a step's status word `flag` stands for, clearing the device word when it is set:
+// EPO_ERR_INTERNAL for a gather cell outside its map (debug builds; the first one is named),
+// EPO_ERR_NUMERIC for a non-finite loss, gradient or pose.
+epo_status flag_status(epo_scene* S, int32_t flag, const char* numeric_msg) {
+  if (!(flag & kFlagRefuse)) return EPO_OK;
+  int32_t dbg[3] = {-1, 0, 0};
+  if (flag & kFlagBounds) {
+    cudaError_t e = cudaMemcpyAsync(dbg, S->d_dbg, 12, cudaMemcpyDeviceToHost, S->stream);
+    if (e != cudaSuccess) return cuda_fail(S, e, "cudaMemcpyAsync");
+    e = cudaMemsetAsync(S->d_dbg, 0xff, 16, S->stream);
+    if (e != cudaSuccess) return cuda_fail(S, e, "cudaMemsetAsync");
+  }
+  cudaError_t e = cudaMemsetAsync(S->d_flag, 0, 4, S->stream);
+  if (e != cudaSuccess) return cuda_fail(S, e, "cudaMemsetAsync");
+  epo_status st = host_wait(S);
+  if (st != EPO_OK) return st;
+  if (flag & kFlagBounds)
+    return fail(S, EPO_ERR_INTERNAL,
+                "a gather cell outside its map (pair " + std::to_string(dbg[0]) + ", cell " + std::to_string(dbg[1]) +
+                    ", " + std::to_string(dbg[2]) + "); its sample was skipped and the poses were not updated");
+  return fail(S, EPO_ERR_NUMERIC, numeric_msg);
+}
 
 // Waits until the work queued before ev_wait has finished: without a limit by blocking on
 // the event, with one by polling it until the limit runs out (EPO_ERR_TIMEOUT; the work stays
@@ -509,6 +535,8 @@ EdgeArgs edge_args(epo_scene* S) {
   }
   a.pair_lw = S->d_pair_lw;
   a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
+  a.flag = S->d_flag;
+  a.dbg = S->d_dbg;
   return a;
 }
 
@@ -1063,6 +1091,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     CK(cudaMemsetAsync(S->d_qoverflow, 0, 4, st));
     CK(cudaMemsetAsync(S->d_step, 0, 8, st));
     CK(cudaMemsetAsync(S->d_flag, 0, 4, st));
+    ALLOC(S->d_dbg, 4);
+    CK(cudaMemsetAsync(S->d_dbg, 0xff, 16, st));
     CK(cudaMemsetAsync(S->d_done, 0, 8, st));
     CK(cudaMemsetAsync(S->d_scene_done, 0, 4 * (size_t)n_scenes, st));
     CK(cudaMemcpyAsync(S->d_loss_chunk_off, chunk_off.data(), chunk_off.size() * 4, cudaMemcpyHostToDevice, st));
@@ -1480,13 +1510,7 @@ epo_status epo_loss_and_grad(epo_scene_t S, double* loss, double* grad) {
   if (st != EPO_OK) return st;
   memcpy(loss, S->h_out, ns * 8);
   if (grad) memcpy(grad, S->h_out + ns, 6 * nv * 8);
-  if (*S->h_flag & 1) {
-    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    st = host_wait(S);
-    if (st != EPO_OK) return st;
-    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient");
-  }
-  return EPO_OK;
+  return flag_status(S, *S->h_flag, "non-finite loss or gradient");
 }
 
 epo_status epo_pair_stats(epo_scene_t S, double* stats) {
@@ -1574,13 +1598,7 @@ epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, doubl
   if (loss) memcpy(loss, S->h_io + 12 * nv, (size_t)S->n_scenes * 8);
   int32_t flag;
   memcpy(&flag, S->h_io + 12 * nv + S->n_scenes, 4);
-  if (flag & 1) {
-    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    st = host_wait(S);
-    if (st != EPO_OK) return st;
-    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
-  }
-  return EPO_OK;
+  return flag_status(S, flag, "non-finite loss or gradient: pose update refused");
 }
 
 epo_status epo_check(epo_scene_t S) {
@@ -1589,13 +1607,7 @@ epo_status epo_check(epo_scene_t S) {
   CK(cudaMemcpyAsync(S->h_flag, S->d_flag, 4, cudaMemcpyDeviceToHost, S->stream));
   epo_status st = host_wait(S);
   if (st != EPO_OK) return st;
-  if (*S->h_flag & 1) {
-    CK(cudaMemsetAsync(S->d_flag, 0, 4, S->stream));
-    st = host_wait(S);
-    if (st != EPO_OK) return st;
-    return fail(S, EPO_ERR_NUMERIC, "non-finite loss or gradient: pose update refused");
-  }
-  return EPO_OK;
+  return flag_status(S, *S->h_flag, "non-finite loss or gradient: pose update refused");
 }
 
 epo_status epo_last_loss(epo_scene_t S, double* loss) {

@@ -167,6 +167,9 @@ __device__ void exact_eval(const EdgeArgs& a, const AmbEntry& en, int64_t rec, d
   y0 = min(y0, P.H - 2);
   const double sa = fma(-(double)x0, Y3, su), sb = fma(-(double)y0, Y3, sv);  // Y3 (u' - x0), Y3 (v' - y0)
   float f00, f01, f10, f11;
+#ifdef EPO_DEBUG_BOUNDS
+  if (!debug_cell_ok(a, p, P.W, P.H, x0, y0)) return;
+#endif
   taps<MAP, GATHER_LDG>(a.map, P.map_off, P.pitch, 0ull, x0, y0, f00, f01, f10, f11);
   const float caf = (float)sa * rz, cbf = (float)sb * rz;  // relative error < 3e-7
   const float top = fmaf(caf, f01 - f00, f00), bot = fmaf(caf, f11 - f10, f10);
@@ -364,6 +367,11 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
         }
         // phase B: all gathers in flight together
         float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
+#ifdef EPO_DEBUG_BOUNDS
+  #pragma unroll
+        for (int r = 0; r < ILP; ++r)
+          if (ok[r] && !debug_cell_ok(a, p, P.W, P.H, x0[r], y0[r])) ok[r] = false;
+#endif
   #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           if (ok[r]) {
@@ -676,6 +684,11 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
         }
         // all gathers in flight together.  A sample that is not fetched gets unspecified tap
         // values, which it never accumulates
+#ifdef EPO_DEBUG_BOUNDS
+#pragma unroll
+        for (int r = 0; r < ILP; ++r)
+          if (fetch[r] && !debug_cell_ok(a, P.p, P.W, P.H, (int)fu1[r] - 1, (int)fv1[r] - 1)) fetch[r] = ok[r] = false;
+#endif
         float m00[ILP], m01[ILP], m10[ILP], m11[ILP];
 #pragma unroll
         for (int r = 0; r < ILP; ++r) {

@@ -73,6 +73,13 @@ __device__ __forceinline__ void griddep_launch_dependents() { asm volatile("grid
 constexpr int kPP64 = 24;
 
 constexpr int kAcc = 8;         // per-pair accumulator slots: sum rho, n_valid, sum gY (3), sum Y x gY (3)
+
+// Bits of the device status word: a non-finite loss, gradient or pose (EPO_ERR_NUMERIC), and, in
+// builds with EPO_DEBUG_BOUNDS, a gather cell outside its map (EPO_ERR_INTERNAL).  A step that
+// starts with either bit set does not update the poses.
+constexpr int kFlagNumeric = 1;
+constexpr int kFlagBounds = 2;
+constexpr int kFlagRefuse = kFlagNumeric | kFlagBounds;
 constexpr int kLossChunk = 32;  // pairs per loss block of the pose kernel (one per lane)
 
 enum Mode { MODE_FWD = 0, MODE_BWD = 1, MODE_FUSED = 2 };
@@ -166,7 +173,29 @@ struct EdgeArgs {
                                  // invalid (fused pass of refine scenes; at PairParam::dbase + r)
   const double* pair_lw;         // n_pairs: the pair's weight in its scene's loss
   int32_t norm_all;
+  int32_t* flag;                 // the status word (kFlag* bits)
+  int32_t* dbg;                  // EPO_DEBUG_BOUNDS builds: the first out-of-map gather (pair, x0, y0)
 };
+
+#ifdef EPO_DEBUG_BOUNDS
+#ifndef EPO_DEBUG_BOUNDS_MARGIN
+#define EPO_DEBUG_BOUNDS_MARGIN 0
+#endif
+// Debug builds: a gather's cell (x0, y0) must lie in [0, W - 2] x [0, H - 2].  A cell outside is
+// recorded (status bit kFlagBounds, the first offender's pair and cell) and its fetch is skipped,
+// so that the step reports EPO_ERR_INTERNAL instead of reading outside the map.  A test build may
+// narrow the accepted range by EPO_DEBUG_BOUNDS_MARGIN columns, so that the report path runs on
+// valid inputs without any access outside a map.
+__device__ __forceinline__ bool debug_cell_ok(const EdgeArgs& a, int p, int W, int H, int x0, int y0) {
+  if (x0 >= 0 && y0 >= 0 && x0 <= W - 2 - EPO_DEBUG_BOUNDS_MARGIN && y0 <= H - 2) return true;
+  if (atomicCAS(a.dbg, -1, p) == -1) {
+    a.dbg[1] = x0;
+    a.dbg[2] = y0;
+  }
+  atomicOr(a.flag, kFlagBounds);
+  return false;
+}
+#endif
 
 // One (pair, role) entry of a pose's gradient gather, laid out at a fixed stride per pose so
 // that the pose kernel reads it without an offset table; p < 0 marks padding.  The pair's

@@ -189,7 +189,7 @@ __device__ __forceinline__ double cross_entry(int r, int c, double w0, double w1
 __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_grad, int n_pose_blocks) {
   static_assert(kPoseThreads == 32 && kLossChunk == 32, "one warp per block, one pair per lane");
   const int64_t step = *a.step;
-  const int flag0 = *a.flag;
+  int flag0 = *a.flag;
   bool bad_here = false;  // this thread set the non-finite flag in this step
   if ((int)blockIdx.x < n_pose_blocks) {
     const int lane = threadIdx.x & 31;
@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
     // the state loads above do not depend on the edge kernel; the pair sums below do
     griddep_wait();
+    flag0 |= *reinterpret_cast<volatile const int*>(a.flag) & kFlagBounds;  // set by the edge kernel
     // the lane's partial sums: dL/dxi_v (six components), then (refine scenes) dL/dgamma_v
     // before its 1 / (1 + gamma_v) factor, then a zero pad
     double g[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
         if (!isfinite(Gg)) {
           atomicOr(a.flag, 1);
           bad_here = true;
-        } else if (!(flag0 & 1) && !conv) {
+        } else if (!(flag0 & kFlagRefuse) && !conv) {
           const double m = a.beta1 * mg_old + (1.0 - a.beta1) * Gg;
           const double vm = a.beta2 * vg_old + (1.0 - a.beta2) * Gg * Gg;
           a.mg[v] = m;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       const bool bad = vv && e < 6 && !isfinite(G);
       const unsigned badmask = __ballot_sync(0xffffffffu, bad);
       // under the pose MLP the poses come from its forward kernel: only the gradient is formed
-      const bool skip = !vv || (flag0 & 1) || a.fixed[v] || conv || a.pose_mlp || ((badmask >> base) & 0xffffu);
+      const bool skip = !vv || (flag0 & kFlagRefuse) || a.fixed[v] || conv || a.pose_mlp || ((badmask >> base) & 0xffffu);
       double xi = 0.0;
       if (!skip && e < 6) {
         const size_t o = 6 * (size_t)v + e;
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     // scene (one pair per lane, fixed shuffle tree); the scene's last chunk to finish adds
     // the scene's partial sums in a fixed order, so the loss does not depend on timing
     griddep_wait();  // the pair sums come from the edge kernel
+    flag0 |= *reinterpret_cast<volatile const int*>(a.flag) & kFlagBounds;
     const int c = blockIdx.x - n_pose_blocks;
     const int s = a.loss_chunk_scene[c];
     const int2 range = a.loss_chunk_pairs[c];
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
       const unsigned long long add = 1ull + (bad_block ? (1ull << 32) : 0ull);
       const unsigned long long prev = atomicAdd(a.done, add);
       if ((unsigned int)prev == gridDim.x - 1) {
-        if (!(flag0 & 1) && ((prev + add) >> 32) == 0ull) {
+        if (!(flag0 & kFlagRefuse) && ((prev + add) >> 32) == 0ull) {
           *a.step = step + 1;
           a.bpow[0] *= a.beta1;
           a.bpow[1] *= a.beta2;
