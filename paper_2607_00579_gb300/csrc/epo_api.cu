@@ -1167,13 +1167,11 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
         q.tex = th[S->pair_dst[p]];
         // the pose-only kernel's bound: with |xn| <= max(cx + 1, W - cx) / fx for a sample
         // within one pixel of the image, |du'| <= fx |1/Y3| E (1 + |xn|) x 2 (safety) + cu,
-        // and the same for v'; Gb = 1/8 / (fx + fy + W + H) keeps t below 1/4 + cb there and,
-        // for a sample farther out, below its distance to the image
+        // and the same for v'
         const double bu = (double)vj.fx + std::max((double)vj.cx + 1.0, (double)vj.W - (double)vj.cx);
         const double bv = (double)vj.fy + std::max((double)vj.cy + 1.0, (double)vj.H - (double)vj.cy);
         q.Kb = (float)(2.0 * std::max(bu, bv) * (1.0 + 1e-6));
         q.cb = std::max(q.cu, q.cv);
-        q.Gb = (float)(0.125 / ((double)vj.fx + (double)vj.fy + (double)vj.W + (double)vj.H));
         q.Wm2 = (float)(vj.W - 2);
         q.Hm2 = (float)(vj.H - 2);
         q.Wf = (float)vj.W;

@@ -543,10 +543,12 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // cell 0 <= x0 <= W - 2, 0 <= y0 <= H - 2 (unsigned compares of the non-negative float bits)
 // and farther than t from every integer has the cell, the border decision and the depth
 // decision of the exact evaluation.  Samples within t of an integer that land within one
-// pixel of the image, within E of the depth threshold, or whose E |1/Y3| exceeds Gb (where
-// the bound stops holding; measured never on the workloads), go to the exact path; samples
-// within the clamp's bound of lambda too, as in k_edge.  Records past the tile's end carry
-// NaN coordinates, so that every comparison on them is false.
+// pixel of the image, within E of the depth threshold, or whose t exceeds 1/4 go to the exact
+// path; samples within the clamp's bound of lambda too, as in k_edge.  The 1/4 cap makes the
+// samples left out safe: with t <= 1/4, E |1/Y3| <= 1/(4 Kb), and a sample that FP32 puts a
+// distance s >= 1 outside the image (it is dropped) has an error of at most
+// 1/4 + s / 4 < s, however large its |xn|, so it is outside in the exact evaluation too.
+// Records past the tile's end carry NaN coordinates, so that every comparison on them is false.
 // ------------------------------------------------------------------------------------
 // Registers per thread: 56 keeps nine 128-thread blocks per SM (measured on the 16-scene batch:
 // 48 and 64 were no faster at four records per thread).  A variant build may set another cap.
@@ -555,9 +557,8 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 #else
 #define EPO_POSE_BOUNDS __maxnreg__(56)
 #endif
-// The exact path for one sample of a pose-only scene, reloading its record: a call (not inlined)
-// from the rare places that need it inside the sample loop, so that its FP64 registers do not
-// count against the loop's.
+// The exact path for one buffered sample of a pose-only scene, reloading its record (a call,
+// not inlined, so that its FP64 registers do not count against the kernel's).
 template <int MODE, int REC, int MAP>
 __device__ __noinline__ void exact_eval_rec(const EdgeArgs& a, int64_t rec, int p, int q, double lam, float lamf) {
   float u, v, z;

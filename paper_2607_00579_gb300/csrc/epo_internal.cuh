@@ -127,9 +127,9 @@ struct alignas(16) PairParam {
   int64_t dbase;          // refine scenes: dzr[dbase + r] holds d(rho)/dz of record r for this pair
   // the pose-only kernel's single rounding bound (scene creation): for a sample whose FP32
   // position lies within one pixel of the target image, |u' - u'(exact)| and |v' - v'(exact)|
-  // are at most t = E |1/Y3| Kb + cb, with E the bound on the error of each component of Y;
-  // a sample with E |1/Y3| > Gb is re-evaluated exactly wherever it lands
-  float Kb, cb, Gb;
+  // are at most t = E |1/Y3| Kb + cb, with E the bound on the error of each component of Y
+  float Kb, cb;
+  float pad0_;
   float Wm2, Hm2;         // W - 2, H - 2: the cell x0 = floor(u') is valid iff 0 <= x0 <= W - 2
   float Wf, Hf;           // W, H: floor(u') + 1 in [0, W] iff u' lies within one pixel of the image
   float pad_;
