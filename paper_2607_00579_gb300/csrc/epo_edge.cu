@@ -497,6 +497,9 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
       }
     }
     __syncthreads();  // every warp has stored its partial sums for this tile
+    // the exact-path count is read between the two barriers: every append of this tile is done,
+    // and no warp appends for the next tile before the second one
+    const int n_amb = min(s_amb_n, kAmbCap);
     // flush: warps summed in a fixed order, one FP64 atomic per used pair slot
     constexpr int S0 = MODE == MODE_BWD ? 2 : 0;
     constexpr int NS = MODE == MODE_FWD ? 2 : NSLOT - S0;
@@ -516,7 +519,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
     if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
     // exact path: when the buffer holds more than kAmbRun entries, and once more before exiting
-    const int n_amb = min(s_amb_n, kAmbCap);
     if (n_amb > (s_tile < a.n_tiles ? kAmbRun : 0)) {
       for (int k = threadIdx.x; k < n_amb; k += blockDim.x) exact_eval<MODE, REC, MAP, REF>(a, s_amb[k], REF ? s_amb_rec[k] : (int64_t)0, lam64, lam);
       __syncthreads();
@@ -795,7 +797,10 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
       const float sred = warp_reduce_scatter8(acc, lane);
       if (lane < 8) s_part[((size_t)warp * a.max_pairs + (q - pb)) * kAcc + scatter_slot(lane)] = sred;
     }
-    __syncthreads();
+    __syncthreads();  // every warp has stored its partial sums and appended its exact-path samples
+    // the exact-path counts are read between the two barriers: every append of this tile is
+    // done, and no warp appends for the next tile before the second one
+    const int n_amb = min(s_amb_n, kAmbCapPose);
     constexpr int S0 = MODE == MODE_BWD ? 2 : 0;
     constexpr int NS = MODE == MODE_FWD ? 2 : kAcc - S0;
     const int nq = (pe - pb) * NS;
@@ -809,7 +814,6 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
     }
     if (threadIdx.x == 0) s_tile = s_next;
     __syncthreads();
-    const int n_amb = min(s_amb_n, kAmbCapPose);
     if (n_amb > (s_tile < a.n_tiles ? kAmbRunPose : 0)) {
       for (int k = threadIdx.x; k < n_amb; k += blockDim.x) {
         const AmbRef ar = s_amb[k];
@@ -911,10 +915,10 @@ static const void* edge_ptr_rpt(int rpt) {
     return rpt == 2 ? (const void*)k_edge<MODE, REC, MAP, GATHER, 2, 1> : nullptr;
   } else {
     switch (rpt) {
-      case 1: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 1>;
-      case 2: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 2>;
-      case 4: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 4>;
-      case 8: return (const void*)k_edge_pose<MODE, REC, MAP, GATHER, 8>;
+      case 1: return (const void*)edge_kernel_of<MODE, REC, MAP, GATHER, 1, 0>();
+      case 2: return (const void*)edge_kernel_of<MODE, REC, MAP, GATHER, 2, 0>();
+      case 4: return (const void*)edge_kernel_of<MODE, REC, MAP, GATHER, 4, 0>();
+      case 8: return (const void*)edge_kernel_of<MODE, REC, MAP, GATHER, 8, 0>();
       default: return nullptr;
     }
   }
