@@ -1569,26 +1569,38 @@ epo_status epo_step_async(epo_scene_t S, int32_t n_steps) {
   return EPO_OK;
 }
 
+// Copies n doubles from src to dst and returns whether all of them are finite (an exponent
+// field of all ones is an infinity or a NaN): one branch-free pass that the compiler vectorises.
+static bool copy_finite(double* __restrict dst, const double* __restrict src, size_t n) {
+  constexpr uint64_t kExp = 0x7ff0000000000000ull;
+  uint64_t bad = 0;
+  for (size_t k = 0; k < n; ++k) {
+    uint64_t b;
+    memcpy(&b, src + k, 8);
+    memcpy(dst + k, &b, 8);
+    bad |= (uint64_t)((b & kExp) == kExp);
+  }
+  return bad == 0;
+}
+
 epo_status epo_step_host(epo_scene_t S, const double* T_in, double* T_out, double* loss) {
   EPO_RANGE("epo_step_host");
   if (!S) return fail(S, EPO_ERR_INVALID_ARG, "null scene");
   const size_t nv = (size_t)S->n_views;
-  if (T_in) {
-    if (S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "under the pose MLP the poses come from its parameters");
-    for (size_t k = 0; k < 12 * nv; ++k)
-      if (!isfinite(T_in[k])) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
-  }
-  epo_status st = maybe_autotune(S);
+  if (T_in && S->pose_mlp) return fail(S, EPO_ERR_INVALID_ARG, "under the pose MLP the poses come from its parameters");
+  // the staging is pinned and mapped: the step's first kernel reads the poses from it, and its
+  // pose kernel (or a copy kernel after the step's last kernel) writes poses, loss and status
+  // word back into it.  A step left queued by a wait that ran out still uses it: wait for it
+  epo_status st = drain(S);
+  if (st != EPO_OK) return st;
+  // the poses go into the staging and are checked in the same pass (nothing runs for
+  // non-finite ones; the staging is rewritten by the next call)
+  if (T_in && !copy_finite(S->h_in, T_in, 12 * nv)) return fail(S, EPO_ERR_INVALID_ARG, "non-finite pose");
+  st = maybe_autotune(S);
   if (st != EPO_OK) return st;
   const int which = T_in ? 2 : 1;
   st = ensure_graph(S, which);
   if (st != EPO_OK) return st;
-  // the staging is pinned and mapped: the step's pair setup reads the poses from it, and its
-  // pose kernel (or a copy kernel after the step's last kernel) writes poses, loss and status
-  // word back into it.  A step left queued by a wait that ran out still uses it: wait for it
-  st = drain(S);
-  if (st != EPO_OK) return st;
-  if (T_in) memcpy(S->h_in, T_in, 12 * nv * 8);
   CK(cudaGraphLaunch(S->graph_host[which - 1], S->stream));
   st = host_wait(S);
   if (st != EPO_OK) return st;

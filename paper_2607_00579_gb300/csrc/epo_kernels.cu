@@ -922,15 +922,26 @@ cudaError_t launch_poses(const StepArgs& a, int with_grad, cudaStream_t s) {
 // graph (the host-driven step): the GPU reads and writes the host buffer directly, so no copy
 // engine round trip sits on the step's critical path.  Reads use ld.global.cv, so that a line
 // of host memory cached by an earlier step is fetched again.
+// Copies between device memory and the mapped host staging: 16-byte accesses where both
+// sides allow them, one element per thread (a host access waits on the link, so all of them
+// are issued at once rather than in a loop per thread).
 __global__ void __launch_bounds__(256) k_io_copy(const double* src, double* dst, int64_t n) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    dst[k] = __ldcv(src + k);
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = __ldcv(src + k);
+}
+__global__ void __launch_bounds__(256) k_io_copy2(const double2* src, double2* dst, int64_t n2) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n2) dst[k] = __ldcv(src + k);
 }
 
 cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 64);
-  k_io_copy<<<grid, 256, 0, s>>>(src, dst, n);
+  if (((uintptr_t)src | (uintptr_t)dst) % 16 == 0 && n % 2 == 0) {
+    k_io_copy2<<<(unsigned)((n / 2 + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(src),
+                                                              reinterpret_cast<double2*>(dst), n / 2);
+  } else {
+    k_io_copy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+  }
   return cudaGetLastError();
 }
 
