@@ -572,7 +572,16 @@ def test_step_host_equals_separate_calls(ring8, opts):
     B.epo_last_loss(b.handle, lb)
     assert np.abs(Ta - b.get_poses().reshape(-1, 12)).max() < 1e-12
     assert la[0] == pytest.approx(lb[0], rel=1e-12)
-    with pytest.raises(epo.EpoError):
+    # non-finite input poses anywhere in the array are refused before anything runs: the next
+    # step continues from the same state
+    for pos, val in (((0, 0), np.nan), ((-1, -1), np.inf), ((3, 5), -np.inf)):
         bad = T.copy()
-        bad[0, 0] = np.nan
-        B.epo_step_host(a.handle, bad, None, None)
+        bad[pos] = val
+        with pytest.raises(epo.EpoError) as e:
+            B.epo_step_host(a.handle, bad, None, None)
+        assert e.value.status == B.EPO_ERR_INVALID_ARG
+    B.epo_step_host(a.handle, None, Ta, la)
+    b.step(1)
+    B.epo_last_loss(b.handle, lb)
+    assert np.abs(Ta - b.get_poses().reshape(-1, 12)).max() < 1e-12
+    assert la[0] == pytest.approx(lb[0], rel=1e-12)
