@@ -221,6 +221,10 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     }
     // a scene whose schedule has converged keeps its poses
     const bool conv = with_grad == 2 && vv && a.schedule && a.sched_state[2 * a.views[v].scene] == 3;
+    // the pose's entry list is fixed at scene creation: the lane's first entry is read before
+    // the wait, so that only the pair sums' loads follow it
+    const PoseEntry* ent = a.pose_entries + (size_t)(vv ? v : 0) * a.pose_stride;
+    const PoseEntry en0 = (vv && e < a.pose_stride) ? ent[e] : PoseEntry{-1, 0};
     // the state loads above do not depend on the edge kernel; the pair sums below do
     griddep_wait();
     flag0 |= *reinterpret_cast<volatile const int*>(a.flag) & kFlagBounds;  // set by the edge kernel
@@ -228,9 +232,8 @@ __global__ void __launch_bounds__(kPoseThreads) k_poses(StepArgs a, int with_gra
     // before its 1 / (1 + gamma_v) factor, then a zero pad
     double g[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (vv) {
-      const PoseEntry* ent = a.pose_entries + (size_t)v * a.pose_stride;
       for (int k = e; k < a.pose_stride; k += 16) {
-        const PoseEntry en = ent[k];
+        const PoseEntry en = k == e ? en0 : ent[k];
         if (en.p < 0) continue;
         const int p = en.p;
         const bool src = (en.scene_role & 1) != 0;
