@@ -1165,13 +1165,16 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
         q.W = vj.W; q.H = vj.H; q.pitch = vj.pitch;
         q.map_off = vj.map_off;
         q.tex = th[S->pair_dst[p]];
-        // the pose-only kernel's bound: with |xn| <= max(cx + 1, W - cx) / fx for a sample
-        // within one pixel of the image, |du'| <= fx |1/Y3| E (1 + |xn|) x 2 (safety) + cu,
-        // and the same for v'
-        const double bu = (double)vj.fx + std::max((double)vj.cx + 1.0, (double)vj.W - (double)vj.cx);
-        const double bv = (double)vj.fy + std::max((double)vj.cy + 1.0, (double)vj.H - (double)vj.cy);
-        q.Kb = (float)(2.0 * std::max(bu, bv) * (1.0 + 1e-6));
-        q.cb = std::max(q.cu, q.cv);
+        // the pose-only kernel's bound t = E |1/Y3| Kb + cb on the error of u' and v' (the
+        // kernel's header derives it): for a sample within one pixel of the image
+        // |u'* - cx| <= max(cx + 1, W - cx) + 1/4 once t <= 1/4; 1e-5 relative margin
+        const double mu = std::max((double)vj.cx + 1.0, (double)vj.W - (double)vj.cx);
+        const double mv = std::max((double)vj.cy + 1.0, (double)vj.H - (double)vj.cy);
+        const double ku = (double)vj.fx + mu + 0.25, kv = (double)vj.fy + mv + 0.25;
+        const double cu = (double)vj.W + 4.0 * mu + std::fabs((double)vj.cx);
+        const double cv = (double)vj.H + 4.0 * mv + std::fabs((double)vj.cy);
+        q.Kb = (float)(std::max(ku, kv) * (1.0 + 1e-5));
+        q.cb = (float)((double)kU32 * std::max(cu, cv) * (1.0 + 1e-5));
         q.Wm2 = (float)(vj.W - 2);
         q.Hm2 = (float)(vj.H - 2);
         q.Wf = (float)vj.W;

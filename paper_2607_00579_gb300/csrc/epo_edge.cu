@@ -535,23 +535,45 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // a2-a7 for pose-only scenes: the same work items, lift, per-pair reduction, flush and exact
 // path as k_edge, with a leaner per-sample screen.
 //
-// Decisions.  With E = X.w + Et (the bound on the error of each component of Y), one bound
-//   t = E |1/Y3| Kb + cb
-// covers the FP32 error of both u' and v' for every sample within one pixel of the target
-// image (Kb holds the largest |xn| such a sample can have).  With x0 = floor(u'), a = u' - x0
-// (exact in FP32), the sample lies within t of a cell line or the border iff
-// min(a (1 - a), b (1 - b)) <= t (1 - t) (t < 1/2 here), one test for both axes and every
-// integer.  Validity in FP32 is then exact: a sample that is in front by more than E, in a
-// cell 0 <= x0 <= W - 2, 0 <= y0 <= H - 2 (unsigned compares of the non-negative float bits)
-// and farther than t from every integer has the cell, the border decision and the depth
-// decision of the exact evaluation.  Samples within t of an integer that land within one
-// pixel of the image, within E of the depth threshold, or whose t exceeds 1/4 go to the exact
-// path; samples within the clamp's bound of lambda too, as in k_edge.  The 1/4 cap makes the
-// samples left out safe: with t <= 1/4, E |1/Y3| <= 1/(4 Kb), and a sample that FP32 puts a
-// distance s >= 1 outside the image (it is dropped) has an error of at most
-// 1/4 + s / 4 < s, however large its |xn|, so it is outside in the exact evaluation too.
+// Decisions are taken in FP32 wherever a rigorous bound on the sample's rounding error shows
+// them to be those of the exact evaluation.  With u = 2^-24:
+//
+// Error of Y.  Every component of the FP32 Y = R X + t is within
+//   E = X.w + Et,  X.w = u (6 |X0| + 7 |X1| + (4 + rho) z + 2 eps_z),  Et = 4u |t|_1
+// of the exact one (each with a 1e-5 relative margin for the second-order terms), where
+// rho = |cx_i| / fx_i + |cy_i| / fy_i.  The lift rounds the intrinsics, the difference, the
+// quotient and the product (4u relative, and u |cx| z / fx through the rounded cx); the
+// rotation's entries are rounded (u); the FMA chain rounds X0 once, X1 twice, X2 = z and t
+// three times; the translation itself is rounded once.  The 2u eps_z covers the depth test's
+// subtraction against the threshold given in double precision.
+//
+// Error of u' (and v').  With iz = rcp.approx(Y3) (relative error 2u), xn = Y1 iz and
+// u' = fma(fx, xn, cx) in the FP32 intrinsics of view j,
+//   |u' - u'*| <= E |1/Y3| (fx + |u'* - cx|) + u (|u'| + 4 |u' - cx| + |cx|):
+// the first term is fx |Y1/Y3 - Y1*/Y3*|, at most fx E (1 + |xn*|) / |Y3| for components
+// within E, the second the roundings of the product, the reciprocal, the FMA and the
+// intrinsics.  For a sample whose FP32 position lies within one pixel of the image and whose
+// bound is at most 1/4, |u'* - cx| <= max(cx + 1, W - cx) + 1/4, so one bound
+//   t = E |1/Y3| Kb + cb,  Kb = max over the axes of f + max(c + 1, W - c) + 1/4,
+//                          cb = u max over the axes of W + 4 max(c + 1, W - c) + |c|
+// (1e-5 margin, which also covers the FP32 evaluation of t) holds for both coordinates.
+//
+// With x0 = floor(u'), a = u' - x0 (exact in FP32), the sample lies within t of a cell line
+// or the border iff min(a (1 - a), b (1 - b)) <= t (1 - t) (t < 1/2 here), one test for both
+// axes and every integer.  Validity in FP32 is then exact: a sample that is in front by more
+// than E, in a cell 0 <= x0 <= W - 2, 0 <= y0 <= H - 2 (unsigned compares of the non-negative
+// float bits) and farther than t from every integer has the cell, the border decision and the
+// depth decision of the exact evaluation.  Samples within t of an integer that land within
+// one pixel of the image, within E of the depth threshold, or whose t exceeds 1/4 go to the
+// exact path; samples within the clamp's bound of lambda too, as in k_edge.  The 1/4 cap makes
+// the samples left out safe: with t <= 1/4, E |1/Y3| Kb <= 1/4, and a sample that FP32 puts a
+// distance s >= 1 outside the image (it is dropped) has an error of at most (1 + s) / 4 plus
+// the roundings, less than s however large its |xn|, so it is outside in the exact evaluation
+// too.
 // Records past the tile's end carry NaN coordinates, so that every comparison on them is false.
 // ------------------------------------------------------------------------------------
+// u (1 + 1e-5): the lift's rounding bound with its margin
+constexpr float kLiftErr = kU32 * 1.00001f;
 // Registers per thread: 56 keeps nine 128-thread blocks per SM (measured on the 16-scene batch:
 // 48 and 64 were no faster at four records per thread).  A variant build may set another cap.
 #ifdef EPO_POSE_MAXNREG
@@ -609,6 +631,8 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
     const int t = s_tile;
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
+    // the lift's share of the rounding bound: |cx| / fx + |cy| / fy of the source view
+    const float rho = fabsf(vi.cx) / vi.fx + fabsf(vi.cy) / vi.fy;
     // a2: lift once per record into shared memory (coalesced 128-bit record loads)
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -617,8 +641,10 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
         float u, v, z;
         load_record<REC>(a.rec, td.begin + idx, u, v, z);
         const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
-        // rounding-error bound of each component of Y = R X + t: 6u |X|_1 (rotation, lift, FMA)
-        s_X[idx] = make_float4(X0, X1, z, 6.f * kU32 * (fabsf(X0) + fabsf(X1) + fabsf(z)));
+        // the record's part of the bound on every component's rounding error in Y = R X + t
+        // (the pose kernel's header derives it): u (6 |X0| + 7 |X1| + (4 + rho) z + 2 eps_z)
+        s_X[idx] = make_float4(X0, X1, z, kLiftErr * fmaf(6.f, fabsf(X0), fmaf(7.f, fabsf(X1),
+                                                                         fmaf(4.f + rho, z, 2.f * eps_z))));
       } else {
         s_X[idx] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);
       }

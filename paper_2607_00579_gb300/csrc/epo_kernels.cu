@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_pair_setup(StepArgs a, int mo
     a.pp64[kPP64 * (size_t)p + 12 + e] = Bv;  // B (9) then c (3)
     of[e] = vf;
   } else if (e == 15) {
-    out->Et = 4.f * kU32 * (fabsf(t0) + fabsf(t1) + fabsf(t2));
+    out->Et = 4.f * (kU32 * 1.00001f) * (fabsf(t0) + fabsf(t1) + fabsf(t2));
   } else if (e == 13) {
     out->active = act;
   } else if (a.refine && e == 12) {
