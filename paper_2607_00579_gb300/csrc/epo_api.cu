@@ -801,7 +801,8 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       w.map_off = map_off;
       map_off += (int64_t)w.pitch * vd.H;
       w.rec_begin = rec_off;
-      w.pad_ = 0;
+      w.rho = (float)(((double)w.cx == vd.cx ? 0.0 : std::fabs(vd.cx) / vd.fx) +
+                      ((double)w.cy == vd.cy ? 0.0 : std::fabs(vd.cy) / vd.fy));
       const uint8_t* src = (const uint8_t*)vd.records;
       if (vd.n_records > 0 && d.pointers_on_device) {
         tmp.resize((size_t)vd.n_records * rec_size);

@@ -335,9 +335,10 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
   #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
-          const float Y0 = fmaf(P.r[0], X.x, fmaf(P.r[1], X.y, fmaf(P.r[2], X.z, P.t[0])));
-          const float Y1 = fmaf(P.r[3], X.x, fmaf(P.r[4], X.y, fmaf(P.r[5], X.z, P.t[1])));
-          Y2[r] = fmaf(P.r[6], X.x, fmaf(P.r[7], X.y, fmaf(P.r[8], X.z, P.t[2])));
+          // the pose kernel's order (z last), so that both kernels compute the same Y
+          const float Y0 = fmaf(P.r[2], X.z, fmaf(P.r[1], X.y, fmaf(P.r[0], X.x, P.t[0])));
+          const float Y1 = fmaf(P.r[5], X.z, fmaf(P.r[4], X.y, fmaf(P.r[3], X.x, P.t[1])));
+          Y2[r] = fmaf(P.r[8], X.z, fmaf(P.r[7], X.y, fmaf(P.r[6], X.x, P.t[2])));
           // |Y_k - Y_k(exact)| <= E; a record past the tile end has X.w = -inf, so that
           // it is never in front and never ambiguous
           const float E = X.w + P.Et;
@@ -539,13 +540,14 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // them to be those of the exact evaluation.  With u = 2^-24:
 //
 // Error of Y.  Every component of the FP32 Y = R X + t is within
-//   E = X.w + Et,  X.w = u (6 |X0| + 7 |X1| + (4 + rho) z + 2 eps_z),  Et = 4u |t|_1
+//   E = X.w + Et,  X.w = u (8 |X0| + 7 |X1| + (2 + rho) z + 2 eps_z),  Et = 4u |t|_1
 // of the exact one (each with a 1e-5 relative margin for the second-order terms), where
-// rho = |cx_i| / fx_i + |cy_i| / fy_i.  The lift rounds the intrinsics, the difference, the
-// quotient and the product (4u relative, and u |cx| z / fx through the rounded cx); the
-// rotation's entries are rounded (u); the FMA chain rounds X0 once, X1 twice, X2 = z and t
-// three times; the translation itself is rounded once.  The 2u eps_z covers the depth test's
-// subtraction against the threshold given in double precision.
+// rho = |cx_i| / fx_i + |cy_i| / fy_i, a term dropped when cx_i (cy_i) is exact in FP32.  The
+// lift rounds fx, the difference, the quotient and the product (4u relative) and cx (u |cx| z
+// / fx); the rotation's entries are rounded (u); the FMA chain, which takes z (the largest
+// component) last, rounds z once, X1 twice, X0 and t three times; the translation itself is
+// rounded once.  The 2u eps_z covers the depth test's subtraction against the threshold given
+// in double precision.
 //
 // Error of u' (and v').  With iz = rcp.approx(Y3) (relative error 2u), xn = Y1 iz and
 // u' = fma(fx, xn, cx) in the FP32 intrinsics of view j,
@@ -631,8 +633,6 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
     const int t = s_tile;
     const TileDev td = a.tiles[t];
     const ViewDev vi = a.views[td.view];
-    // the lift's share of the rounding bound: |cx| / fx + |cy| / fy of the source view
-    const float rho = fabsf(vi.cx) / vi.fx + fabsf(vi.cy) / vi.fy;
     // a2: lift once per record into shared memory (coalesced 128-bit record loads)
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -642,9 +642,9 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
         load_record<REC>(a.rec, td.begin + idx, u, v, z);
         const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
         // the record's part of the bound on every component's rounding error in Y = R X + t
-        // (the pose kernel's header derives it): u (6 |X0| + 7 |X1| + (4 + rho) z + 2 eps_z)
-        s_X[idx] = make_float4(X0, X1, z, kLiftErr * fmaf(6.f, fabsf(X0), fmaf(7.f, fabsf(X1),
-                                                                         fmaf(4.f + rho, z, 2.f * eps_z))));
+        // (the pose kernel's header derives it): u (8 |X0| + 7 |X1| + (2 + rho) z + 2 eps_z)
+        s_X[idx] = make_float4(X0, X1, z, kLiftErr * fmaf(8.f, fabsf(X0), fmaf(7.f, fabsf(X1),
+                                                                         fmaf(2.f + vi.rho, z, 2.f * eps_z))));
       } else {
         s_X[idx] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);
       }
@@ -680,9 +680,10 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
 #pragma unroll
         for (int r = 0; r < ILP; ++r) {
           const float4 X = s_X[threadIdx.x + (g + r) * blockDim.x];
-          const float Y0 = fmaf(r0, X.x, fmaf(r1, X.y, fmaf(r2, X.z, t0)));
-          const float Y1 = fmaf(r3, X.x, fmaf(r4, X.y, fmaf(r5, X.z, t1)));
-          const float Y2 = fmaf(r6, X.x, fmaf(r7, X.y, fmaf(r8, X.z, t2)));
+          // z, the largest component of X, enters last (rounded once), X0 and t first
+          const float Y0 = fmaf(r2, X.z, fmaf(r1, X.y, fmaf(r0, X.x, t0)));
+          const float Y1 = fmaf(r5, X.z, fmaf(r4, X.y, fmaf(r3, X.x, t1)));
+          const float Y2 = fmaf(r8, X.z, fmaf(r7, X.y, fmaf(r6, X.x, t2)));
           iz[r] = rcp_approx(Y2);
           xn[r] = Y0 * iz[r];
           yn[r] = Y1 * iz[r];

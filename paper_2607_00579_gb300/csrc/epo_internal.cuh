@@ -96,7 +96,8 @@ struct ViewDev {
   int64_t map_off;        // element offset of the map in the atlas
   int64_t rec_begin;      // first record of the view
   int32_t n_rec;          // records kept
-  int32_t pad_;
+  float rho;              // the lift's share of the rounding bound through the rounded principal
+                          // point: |cx| / fx + |cy| / fy, each term 0 when cx (cy) is exact in FP32
 };
 
 struct TileDev {
