@@ -75,6 +75,7 @@ struct epo_scene {
   // device buffers
   std::vector<DevBuf> bufs;
   void* d_rec = nullptr;
+  float4* d_lift = nullptr;  // pose-only scenes: the records lifted once (EdgeArgs::lift)
   void* d_map = nullptr;
   int64_t map_elems = 0;
   ViewDev* d_views = nullptr;
@@ -537,6 +538,7 @@ EdgeArgs edge_args(epo_scene* S) {
   a.norm_all = S->opt.norm_mode == EPO_NORM_ALL;
   a.flag = S->d_flag;
   a.dbg = S->d_dbg;
+  a.lift = S->d_lift;
   return a;
 }
 
@@ -801,8 +803,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       w.map_off = map_off;
       map_off += (int64_t)w.pitch * vd.H;
       w.rec_begin = rec_off;
-      w.rho = (float)(((double)w.cx == vd.cx ? 0.0 : std::fabs(vd.cx) / vd.fx) +
-                      ((double)w.cy == vd.cy ? 0.0 : std::fabs(vd.cy) / vd.fy));
+      w.pad_ = 0;
       const uint8_t* src = (const uint8_t*)vd.records;
       if (vd.n_records > 0 && d.pointers_on_device) {
         tmp.resize((size_t)vd.n_records * rec_size);
@@ -885,6 +886,7 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
     e = cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(S, e, "cudaStreamCreate");
     ALLOC(*(uint8_t**)&S->d_rec, std::max<size_t>(rec_host.size(), 16));
+    if (!S->refine) ALLOC(S->d_lift, std::max<int64_t>(S->n_records, 1));
     {
       uint8_t* raw = nullptr;
       ALLOC(raw, (size_t)S->map_elems * map_size + 512);
@@ -1088,6 +1090,9 @@ epo_status create_impl(int32_t n_scenes, const epo_scene_desc* descs, const epo_
       }
       CK(cudaMemcpy(S->d_K64, K64.data(), K64.size() * 8, cudaMemcpyHostToDevice));
     }
+    // the intrinsics and depths of a pose-only scene stay fixed: its records are lifted once
+    if (S->d_lift)
+      CK(launch_lift_records(S->d_rec, S->rec_dtype, S->d_views, S->d_K64, (int)nv, (float)o.eps_z, S->d_lift, st));
     CK(cudaMemsetAsync(S->d_qcount, 0, 4, st));
     CK(cudaMemsetAsync(S->d_qoverflow, 0, 4, st));
     CK(cudaMemsetAsync(S->d_step, 0, 8, st));

@@ -540,14 +540,12 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // them to be those of the exact evaluation.  With u = 2^-24:
 //
 // Error of Y.  Every component of the FP32 Y = R X + t is within
-//   E = X.w + Et,  X.w = u (8 |X0| + 7 |X1| + (2 + rho) z + 2 eps_z),  Et = 4u |t|_1
-// of the exact one (each with a 1e-5 relative margin for the second-order terms), where
-// rho = |cx_i| / fx_i + |cy_i| / fy_i, a term dropped when cx_i (cy_i) is exact in FP32.  The
-// lift rounds fx, the difference, the quotient and the product (4u relative) and cx (u |cx| z
-// / fx); the rotation's entries are rounded (u); the FMA chain, which takes z (the largest
-// component) last, rounds z once, X1 twice, X0 and t three times; the translation itself is
-// rounded once.  The 2u eps_z covers the depth test's subtraction against the threshold given
-// in double precision.
+//   E = X.w + Et,  X.w = u (5 |X0| + 4 |X1| + 2 z + 2 eps_z),  Et = 4u |t|_1
+// of the exact one (each with a 1e-5 relative margin for the second-order terms).  The records
+// are lifted once at scene creation in FP64 and rounded (u |X|); the rotation's entries are
+// rounded (u); the FMA chain, which takes z (the largest component) last, rounds z once, X1
+// twice, X0 and t three times; the translation itself is rounded once.  The 2u eps_z covers the
+// depth test's subtraction against the threshold given in double precision.
 //
 // Error of u' (and v').  With iz = rcp.approx(Y3) (relative error 2u), xn = Y1 iz and
 // u' = fma(fx, xn, cx) in the FP32 intrinsics of view j,
@@ -574,8 +572,6 @@ __global__ void __launch_bounds__(512) k_edge(EdgeArgs a) {
 // too.
 // Records past the tile's end carry NaN coordinates, so that every comparison on them is false.
 // ------------------------------------------------------------------------------------
-// u (1 + 1e-5): the lift's rounding bound with its margin
-constexpr float kLiftErr = kU32 * 1.00001f;
 // Registers per thread: 56 keeps nine 128-thread blocks per SM (measured on the 16-scene batch:
 // 48 and 64 were no faster at four records per thread).  A variant build may set another cap.
 #ifdef EPO_POSE_MAXNREG
@@ -632,19 +628,13 @@ __global__ void EPO_POSE_BOUNDS k_edge_pose(EdgeArgs a) {
   while (s_tile < a.n_tiles) {
     const int t = s_tile;
     const TileDev td = a.tiles[t];
-    const ViewDev vi = a.views[td.view];
-    // a2: lift once per record into shared memory (coalesced 128-bit record loads)
+    // a2: the tile's records, lifted at scene creation with their share of the rounding bound,
+    // staged in shared memory (coalesced 128-bit loads)
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       const int idx = threadIdx.x + r * blockDim.x;
       if (idx < td.n) {
-        float u, v, z;
-        load_record<REC>(a.rec, td.begin + idx, u, v, z);
-        const float X0 = (u - vi.cx) / vi.fx * z, X1 = (v - vi.cy) / vi.fy * z;
-        // the record's part of the bound on every component's rounding error in Y = R X + t
-        // (the pose kernel's header derives it): u (8 |X0| + 7 |X1| + (2 + rho) z + 2 eps_z)
-        s_X[idx] = make_float4(X0, X1, z, kLiftErr * fmaf(8.f, fabsf(X0), fmaf(7.f, fabsf(X1),
-                                                                         fmaf(2.f + vi.rho, z, 2.f * eps_z))));
+        s_X[idx] = __ldg(a.lift + td.begin + idx);
       } else {
         s_X[idx] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.f);
       }

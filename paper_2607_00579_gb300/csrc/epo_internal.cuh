@@ -96,8 +96,7 @@ struct ViewDev {
   int64_t map_off;        // element offset of the map in the atlas
   int64_t rec_begin;      // first record of the view
   int32_t n_rec;          // records kept
-  float rho;              // the lift's share of the rounding bound through the rounded principal
-                          // point: |cx| / fx + |cy| / fy, each term 0 when cx (cy) is exact in FP32
+  int32_t pad_;
 };
 
 struct TileDev {
@@ -176,6 +175,8 @@ struct EdgeArgs {
   int32_t norm_all;
   int32_t* flag;                 // the status word (kFlag* bits)
   int32_t* dbg;                  // EPO_DEBUG_BOUNDS builds: the first out-of-map gather (pair, x0, y0)
+  const float4* lift;            // pose-only scenes: every record lifted once at creation, (X0, X1,
+                                 // z, the bound on its share of Y's rounding error)
 };
 
 #ifdef EPO_DEBUG_BOUNDS
@@ -369,6 +370,10 @@ cudaError_t launch_apply_left_jacobian(const double* xi, const double* g, double
 cudaError_t launch_map_check(const void* map, int dtype, int64_t n, int32_t* bad, cudaStream_t s);
 cudaError_t launch_edt(const uint8_t* edges, int W, int H, float* map, cudaStream_t s);
 cudaError_t launch_round_bf16(const float* src, uint16_t* dst, int64_t n, cudaStream_t s);
+// a2 for scenes whose intrinsics and depths stay fixed: each kept record's camera-frame point
+// X = z ((u - cx) / fx, (v - cy) / fy, 1) in FP64, rounded to FP32, with its rounding bound
+cudaError_t launch_lift_records(const void* rec, int rec_dtype, const ViewDev* views, const double* K64,
+                                int n_views, float eps_z, float4* out, cudaStream_t s);
 int edt_max_height();
 const void* edge_kernel_ptr(int mode, int refine, int rec_dtype, int map_dtype, int gather, int rpt);
 size_t edge_smem_bytes(int rpt, int block, int max_pairs, int refine);

@@ -948,6 +948,36 @@ cudaError_t launch_io_copy(const double* src, double* dst, int64_t n, cudaStream
   return cudaGetLastError();
 }
 
+// One block per view.  The stored X is within u |X| of the exact point (one rounding of an FP64
+// value); with the rotation's rounded entries and the edge kernel's FMA chain (z taken last),
+// every component of Y = R X + t is then within u (5 |X0| + 4 |X1| + 2 z) + 4u |t|_1 of the exact
+// one, and the depth test's subtraction against the double-precision threshold adds 2u eps_z;
+// the record's share, with a 1e-5 relative margin, is the stored fourth component.
+template <int REC>
+__global__ void __launch_bounds__(256) k_lift_records(const void* rec, const ViewDev* views, const double* K64,
+                                                      float eps_z, float4* out) {
+  const ViewDev vw = views[blockIdx.x];
+  const double* K = K64 + 6 * (size_t)blockIdx.x;
+  const double fx = K[0], fy = K[1], cx = K[2], cy = K[3];
+  for (int k = threadIdx.x; k < vw.n_rec; k += blockDim.x) {
+    const int64_t r = vw.rec_begin + k;
+    float u, v, z;
+    load_record<REC>(rec, r, u, v, z);
+    const float X0 = (float)(((double)u - cx) / fx * (double)z);
+    const float X1 = (float)(((double)v - cy) / fy * (double)z);
+    const float w = (kU32 * 1.00001f) * fmaf(5.f, fabsf(X0), fmaf(4.f, fabsf(X1), fmaf(2.f, z, 2.f * eps_z)));
+    out[r] = make_float4(X0, X1, z, w);
+  }
+}
+
+cudaError_t launch_lift_records(const void* rec, int rec_dtype, const ViewDev* views, const double* K64,
+                                int n_views, float eps_z, float4* out, cudaStream_t s) {
+  if (n_views <= 0) return cudaSuccess;
+  if (rec_dtype == 0) k_lift_records<0><<<n_views, 256, 0, s>>>(rec, views, K64, eps_z, out);
+  else k_lift_records<1><<<n_views, 256, 0, s>>>(rec, views, K64, eps_z, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_twist_poses(const double* T, const double* xi, double* T_out, int n,
                                cudaStream_t s) {
   k_twist_poses<<<(n + 127) / 128, 128, 0, s>>>(T, xi, T_out, n);

@@ -121,15 +121,22 @@ def test_refined_full_size_ring32():
 
 
 def test_refine_scene_steps_like_pose_only_scene(ring8):
+    """The same objective through the refine kernels and the pose-only kernels.  A pose-only
+    scene lifts its records once, in FP64 rounded to FP32; a refine scene lifts them every step
+    in FP32 (its intrinsics and depths change): the two lifted points differ by a few roundings
+    (at most ~5u relative per component), so loss and gradient agree to FP32 rounding, and
+    after 10 Adam steps the poses agree to the amplified rounding of every sample."""
     sc, maps = ring8
     s = refine_scene(sc, maps)
     p = gpu_scene(sc, maps)
     for h in (s, p):
         h.set_poses(sc.T_init)
+    ls, gs = s.loss_and_grad()
+    lp, gp = p.loss_and_grad()
+    assert ls[0] == pytest.approx(lp[0], rel=1e-6) and grad_rel_err(gs, gp) < 1e-5
+    for h in (s, p):
         h.step(10)
-    # the same objective through the refine kernels (see above): after 10 Adam steps the
-    # poses agree to the amplified rounding of those few samples
-    assert np.abs(s.get_poses() - p.get_poses()).max() < 1e-6
+    assert np.abs(s.get_poses() - p.get_poses()).max() < 1e-5
     assert s.info().kernels_per_step == 4
 
 
