@@ -35,7 +35,10 @@
  *     calls suffixed _dev take device pointers and do not synchronise.
  *   - A scene handle is not thread-safe: one host thread at a time.
  *   - epo_create_* copy every input into library-owned device memory; the
- *     caller may free its buffers as soon as the call returns.
+ *     caller may free its buffers as soon as the call returns.  A scene without
+ *     focal or depth refinement also keeps every record lifted to its camera
+ *     frame (16 bytes per record, computed once in double precision), since its
+ *     intrinsics and depths do not change; device_bytes counts it.
  */
 #ifndef EPO_H
 #define EPO_H
