@@ -135,6 +135,31 @@ def test_loss_grad_parity_small_ring(ring8, gather, rpt, block):
     check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=st)
 
 
+@pytest.mark.parametrize("gather,rpt,block", [(epo.EPO_GATHER_TEX, 4, 128), (epo.EPO_GATHER_LDG, 2, 128)])
+def test_off_centre_wide_angle_intrinsics_match_oracle(ring8, gather, rpt, block):
+    """The pose kernel's rounding bound where its terms are largest: a focal length a third of
+    the scene's (|xn| up to ~1.5 at the image edges, so the X0 and X1 terms dominate z's) and
+    principal points far off centre and not exact in FP32 (the projection's |u' - cx| and |cx|
+    terms, and the stored lift's rounding of cx), with the records and maps unchanged: every
+    cell, border and depth decision must still be the exact evaluation's."""
+    import dataclasses
+    sc, maps = ring8
+    K = sc.K.copy()
+    K[:, 0] *= 0.3333331
+    K[:, 1] *= 0.3512347
+    K[:, 2] += 0.31234567 * sc.W
+    K[:, 3] -= 0.27654321 * sc.H
+    sw = dataclasses.replace(sc, K=K)
+    s = gpu_scene(sw, maps, gather=gather, records_per_thread=rpt, block_threads=block)
+    s.set_poses(sc.T_init)
+    loss, grad = s.loss_and_grad()
+    st = s.pair_stats()
+    o = oracle_of(sw, maps).loss_grad(sc.T_init, lam=10.0)
+    # a fair share of the samples still lands in the images
+    assert o["pair_stats"][:, 1].sum() > 0.2 * sum(int(sc.rec_off[i + 1] - sc.rec_off[i]) for i, _ in sc.pairs)
+    check_against_oracle(loss[0], grad, o, sc.pairs, sc.T_init, stats=st)
+
+
 @pytest.mark.parametrize("tail", [1, 2, 3])
 def test_split_last_wave_matches_oracle(ring8, tail):
     """Work items of the last wave split into items of `tail` pairs (on this small scene the
